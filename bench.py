@@ -1,0 +1,331 @@
+"""Benchmark of the fast Slepian projection on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c65k|c1m|c4m|tiny]
+
+A step is one fast projection of the whole batch (plan prebuilt): the FFT
+convolution B y and the rank-r correction S_T (D o S_T^T y), i.e. every step of the
+hot path.  Default workload: N = 65536, W = 1/8, eps = 1e-4, 1024 real FP32
+signals (half N(0,1), half 256-tone band-limited), inputs resident in HBM.
+
+  value         projected samples/s (sum of N over the batch, all ranks) / step time
+  e2e           the same metric through fst_project_host with pinned HOST buffers:
+                host->device copy, projection and device->host copy in the timed region
+  roofline      dominant kernel: algorithmic bytes per launch (2 N s per signal read +
+                written, plus S_T and the spectrum) / its CUDA-event launch time,
+                against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 oracle's fast projection on the host cores, bounded sample
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the oracle (the CPU reference of this build) on the same
+workload, a bounded sample of signals per step, on rank 0 only.
+
+Multi-GPU (torchrun): every rank projects its own batch (weak scaling, no
+collective on the data path); barrier + max over ranks of the step time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c65k": dict(desc="N=65536 W=1/8 eps=1e-4, 1024 real FP32 signals (512 N(0,1), 512 256-tone)",
+                 batch=1024),
+    "c1m": dict(desc="N=2^20 W=0.05 eps=1e-6, 64 complex64 signals (32 CN(0,1), 32 band-limited)",
+                batch=64),
+    "c4m": dict(desc="N=2^22 W=1/4 eps=1e-8, 16 real FP32 signals (8 N(0,1), 8 1024-tone)", batch=16),
+    "tiny": dict(desc="N=4096 W=1/16 eps=1e-6, 2 real signals (N(0,1), 64-tone)", batch=2),
+}
+
+
+def make_workload(name, device, batch=None):
+    from paper_1611_04950_gb300 import workloads as WL
+    if name == "c65k":
+        return WL.c65k(batch=batch or 1024, device=device)
+    if name == "c1m":
+        return WL.c1m(batch=batch or 64, device=device)
+    if name == "c4m":
+        return WL.c4m(batch=batch or 16, device=device)
+    if name == "tiny":
+        return WL.tiny(device=device)
+    raise ValueError(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(wl_name, y_sample, W, eps, K, budget_s=10.0):
+    """Oracle fast projection (FP64, numpy/scipy as written) on host cores; returns
+    (samples/s, threads used, sample description)."""
+    from oracle import fst_oracle as O
+    import numpy as np
+    N = y_sample.shape[1]
+    plan = O.make_plan(N, W, K, eps)
+    y = np.ascontiguousarray(y_sample.T)
+    O.fast_project(plan, y[:, :1])  # warm
+    n_done, t0, c0 = 0, time.perf_counter(), time.process_time()
+    while True:
+        O.fast_project(plan, y)
+        n_done += y.shape[1]
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    threads = max(1, round(cpu / wall))
+    return n_done * N / wall, threads, (f"{y.shape[1]} signals of the {wl_name} workload, repeated "
+                                        f"{n_done // y.shape[1]}x over {wall:.1f} s, plan prebuilt")
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, rank 0 only."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import fst_oracle as O
+    wl = make_workload(args.workload, "cpu", batch=8 if args.workload == "c65k" else None)
+    y = wl.y.numpy()
+    if np.iscomplexobj(y):
+        y = y.astype(np.complex128)
+    else:
+        y = y.astype(np.float64)
+    sample = y[: min(8, y.shape[0])]
+    N = sample.shape[1]
+    K = O.default_K(N, wl.W)
+    plan = O.make_plan(N, wl.W, K, wl.eps)
+    ys = np.ascontiguousarray(sample.T)
+    for _ in range(args.warmup):
+        O.fast_project(plan, ys)
+    times = []
+    c0, t0 = time.process_time(), time.perf_counter()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.fast_project(plan, ys)
+        times.append(time.perf_counter() - t)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    step = sum(times) / len(times)
+    value = sample.shape[0] * N / step
+    line = {
+        "impl": "reference", "metric": "projected samples/s", "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]["desc"],
+                                         "sample_signals_per_step": int(sample.shape[0])},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": max(1, round(cpu / wall)),
+                         "kind": "oracle",
+                         "sample": f"{sample.shape[0]} signals of the workload per step, FP64 oracle fast "
+                                   f"projection, plan prebuilt"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c65k", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1611_04950_gb300 import fst as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = make_workload(args.workload, "cuda", args.batch)
+    y = wl.y.contiguous()
+    out = torch.empty_like(y)
+    B, N = y.shape
+    plan = F.Plan(N, wl.W, eps=wl.eps)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.project(y, out)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = F.fst_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.project(y, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = F.fst_launch_count() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    samples_per_step = B * N * world
+    value = samples_per_step / (ms * 1e-3)
+
+    # per-kernel launch times (separate pass with events around every launch)
+    F.fst_profile_enable(True)
+    for _ in range(3):
+        plan.project(y, out)
+    torch.cuda.synchronize()
+    recs = F.fst_profile_records()
+    F.fst_profile_enable(False)
+    per = {}
+    for name, t_ms, units in recs:
+        d = per.setdefault(name, {"launches": 0, "ms": 0.0, "pairs": 0})
+        d["launches"] += 1
+        d["ms"] += t_ms
+        d["pairs"] += units
+    tot = sum(d["ms"] for d in per.values()) or 1.0
+    dom = max(per, key=lambda k: per[k]["ms"])
+    dd = per[dom]
+    peaks, peak_src = measured_peaks()
+    sig_bytes = N * (8 if y.is_complex() else 4)          # bytes of one signal
+    pairs_per_launch = dd["pairs"] / dd["launches"]
+    signals_per_launch = pairs_per_launch * (1 if y.is_complex() else 2)
+    alg_bytes = signals_per_launch * 2 * sig_bytes + N * plan.r * 4 + plan.M * 4
+    launch_ms = dd["ms"] / dd["launches"]
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_source": peak_src,
+                "kernels": {k: {"launches": v["launches"] // 3, "ms_per_step": v["ms"] / 3,
+                                "share": v["ms"] / tot} for k, v in per.items()}}
+    # whole path against the same roofline (all kernels of one step)
+    step_alg = B * 2 * sig_bytes + N * plan.r * 4 + plan.M * 4
+    roofline["path_frac"] = step_alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        yh = y.cpu().pin_memory()
+        oh = torch.empty_like(yh).pin_memory()
+        plan.project_host(yh, oh)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        k2 = max(3, args.steps // 2)
+        for _ in range(k2):
+            plan.project_host(yh, oh)
+        ee1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / k2
+        if world > 1:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        nbytes = B * sig_bytes
+        e2e = {"value": samples_per_step / wall, "unit": "samples/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": wall * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ys = y[: min(8, B)].cpu()
+        ys = ys.to(torch.complex128) if ys.is_complex() else ys.double()
+        rate, threads, sample = cpu_oracle_rate(args.workload, ys.numpy(), wl.W, wl.eps, plan.K)
+        cpu = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "projected samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if y.is_complex() else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "N": N, "W": wl.W, "eps": wl.eps,
+                       "batch_per_gpu": B, "K": plan.K, "r": plan.r, "M": plan.M,
+                       "l2": f"inputs {B * sig_bytes / 2**20:.0f} MiB + outputs of the same size exceed "
+                             f"the 129 MB L2; no flush"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

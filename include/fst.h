@@ -1,0 +1,186 @@
+/*
+ * fst.h -- C ABI of the GB300 fast Slepian projection library (libfst_gb300.so).
+ *
+ * The library computes the fast approximation of S_K S_K^* y of Corollary 2 and
+ * Section 1.3 ("Fast projections onto the range of S_K") of Karnik, Zhu, Wakin,
+ * Romberg, Davenport, "The Fast Slepian Transform" (arXiv:1611.04950):
+ *
+ *     P_fast y = B_{N,W} y + S_T (D o (S_T^T y)),
+ *
+ * where B_{N,W} is the prolate matrix (Eq. "Prolate matrix", Section 1.2) applied as
+ * a zero-padded length-M FFT convolution (M = smallest power of two >= 2N,
+ * Section 4.1), S_T holds the Slepian basis vectors whose eigenvalues lie in the
+ * transition band, and D = 1[l<K] - lambda_l (the U1 U2^* factors of the proof of
+ * Corollary 2).  The same machinery gives the truncated pseudoinverse of B
+ * (Corollary 3, D = 1/lambda - lambda on l<K, -lambda on l>=K) and the Tikhonov
+ * operator (Corollary 4, B/(1+alpha) + U5 U5^*).
+ *
+ * Conventions for every entry point:
+ *   - Status codes are returned; the library never aborts.  fst_last_error() gives
+ *     a message for the last failing call on the calling host thread.
+ *   - Device pointers are caller-owned CUDA device memory; the library never frees
+ *     them.  Host pointers are plain host memory (pinned memory copies faster).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All device
+ *     work of a call is enqueued on it; calls return before the work completes
+ *     unless stated otherwise.
+ *   - Signals are stored one after another: signal b starts at element b*ld
+ *     (ld >= N; ld = 0 means ld = N).  Real dtypes hold N reals per signal,
+ *     complex dtypes N interleaved (re, im) pairs.
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the caller
+ *     (they share the plan's device workspace).
+ */
+#ifndef FST_GB300_H
+#define FST_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fst_plan_s *fst_plan_t;
+
+typedef enum {
+  FST_OK = 0,
+  FST_EINVAL = 1,          /* an argument is out of range                       */
+  FST_ENOMEM = 2,          /* device or host allocation failed                  */
+  FST_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed       */
+  FST_ENOCONVERGE = 4,     /* plan-time eigen-solver did not converge           */
+  FST_ETIMEOUT = 5,        /* a bounded device wait gave up                     */
+  FST_EUNSUPPORTED = 6     /* valid request this build does not handle          */
+} fst_status;
+
+typedef enum {
+  FST_F32 = 0,   /* real float32        */
+  FST_F64 = 1,   /* real float64        */
+  FST_C64 = 2,   /* complex float32 (interleaved re, im) */
+  FST_C128 = 3   /* complex float64 (interleaved re, im) */
+} fst_dtype;
+
+typedef enum {
+  FST_OP_PROJECT = 0,   /* S_K S_K^*                   (Corollary 2) */
+  FST_OP_PINV = 1,      /* rank-K truncated B^dagger   (Corollary 3) */
+  FST_OP_TIKHONOV = 2   /* (B^2 + alpha I)^{-1} B      (Corollary 4) */
+} fst_op;
+
+/*
+ * fst_plan -- precomputation of Section 1.3 (last paragraph) and Section 4.1.
+ * Computes, on the GPU in FP64, the Slepian basis vectors of the eigen-window
+ * around K (bisection on Slepian's commuting tridiagonal matrix, split by parity,
+ * then inverse iteration), their eigenvalues lambda_l = s_l^T B s_l (FP64 FFT
+ * convolution), the transition set T = {l : |1[l<K] - lambda_l| > eps}, D, the
+ * real sinc spectrum DFT_M(c) (FP64, stored FP32 and FP64) and the twiddle tables.
+ *   out     receives the new plan (owned by the library; free with fst_destroy).
+ *   N       signal length, 1 <= N <= 2^23.
+ *   W       half-bandwidth, 0 < W < 1/2.
+ *   K       number of Slepian vectors kept, 0 <= K <= N; K < 0 selects
+ *           round(2NW) with halves rounded away from zero (Section 4.1).
+ *   eps     tolerance, 0 < eps < 1/2 (Theorem 1, Corollary 2).
+ *   stream  stream for the plan-time kernels; the call synchronises it.
+ * K need not satisfy the band condition of Corollary 2; T then grows.
+ * Errors: FST_EINVAL, FST_ENOMEM, FST_ECUDA, FST_ENOCONVERGE.
+ */
+fst_status fst_plan(fst_plan_t *out, int64_t N, double W, int64_t K, double eps,
+                    void *stream);
+
+/*
+ * fst_plan_op -- as fst_plan, for the operator `op` (fst_op).  alpha is the
+ * Tikhonov parameter (> 0, FST_OP_TIKHONOV only; ignored otherwise).  For
+ * Tikhonov the transition set is {alpha(1+alpha)eps < lambda < 1 - eps/3}
+ * (Corollary 4) and the Toeplitz part is scaled by 1/(1+alpha).
+ */
+fst_status fst_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, double eps,
+                       int op, double alpha, void *stream);
+
+/*
+ * fst_plan_info -- sizes of a plan.  Any output pointer may be NULL.
+ *   K, r (= |T|), M (FFT length), window_lo / window_hi (eigen-window searched,
+ *   inclusive descending-lambda indices).
+ */
+fst_status fst_plan_info(fst_plan_t plan, int64_t *K, int64_t *r, int64_t *M,
+                         int64_t *window_lo, int64_t *window_hi);
+
+/*
+ * fst_plan_export -- copies the plan's transition data to HOST arrays (any may be
+ * NULL): idx[r] (int64 indices l in T, ascending), lam[r] (lambda_l, FP64),
+ * D[r] (FP64), S_T[N*r] (FP64, column j = s^(idx[j]) contiguous, unit norm).
+ * Synchronous.
+ */
+fst_status fst_plan_export(fst_plan_t plan, int64_t *idx, double *lam, double *D,
+                           double *S_T);
+
+/*
+ * fst_project -- P_fast y for `batch` signals resident on the device
+ * (Section 1.3, "Fast projections onto the range of S_K").
+ *   y, out  device pointers, `batch` signals each, stride ld (0 = N).  y and out
+ *           may be equal (in place); otherwise they must not overlap.
+ *   dtype   FST_F32 / FST_C64: FP32 FFT convolution and FP32 correction;
+ *           FST_F64 / FST_C128: the same kernels in FP64.
+ * Real signals are processed two at a time as the real and imaginary parts of
+ * one complex FFT (B and S_T are real, so they do not mix).
+ * Errors: FST_EINVAL (NULL pointer, batch < 0, ld < N), FST_ENOMEM, FST_ECUDA.
+ * batch == 0 is a no-op returning FST_OK.
+ */
+fst_status fst_project(fst_plan_t plan, const void *y, void *out, int64_t batch,
+                       int64_t ld, int dtype, void *stream);
+
+/*
+ * fst_project_host -- as fst_project, with y and out in HOST memory (contiguous,
+ * ld = N).  The batch is copied to the device, projected and copied back in
+ * chunks on `stream`, overlapping copies with compute; returns after the result
+ * is in `out` (synchronous).
+ */
+fst_status fst_project_host(fst_plan_t plan, const void *y, void *out, int64_t batch,
+                            int dtype, void *stream);
+
+/*
+ * fst_apply_prolate -- B_{N,W} y alone (no correction): the Toeplitz product of
+ * Eq. "Prolate matrix" by the plan's FFT convolution.  Same arguments as
+ * fst_project.
+ */
+fst_status fst_apply_prolate(fst_plan_t plan, const void *y, void *out, int64_t batch,
+                             int64_t ld, int dtype, void *stream);
+
+/* fst_destroy -- frees the plan and its device memory.  NULL-safe. */
+fst_status fst_destroy(fst_plan_t plan);
+
+/* fst_last_error -- message of the last failing call on this host thread ("" if none). */
+const char *fst_last_error(void);
+
+/* fst_version -- library version string. */
+const char *fst_version(void);
+
+/*
+ * fst_reduced_tridiagonal -- HOST-only helper exposing the plan's parity split of
+ * Slepian's tridiagonal matrix (used by the plan's bisection; exported so the
+ * split can be checked without a GPU).  parity 0: symmetric vectors, size
+ * ceil(N/2); parity 1: antisymmetric vectors, size floor(N/2).  Writes the size to
+ * *n, the diagonal to d[0..n) and the off-diagonal to e[0..n-1) (either array may
+ * be NULL to query the size).  The l-th largest eigenvalue of the full matrix is
+ * the (l div 2)-th largest of the parity-(l mod 2) matrix.
+ */
+fst_status fst_reduced_tridiagonal(int64_t N, double W, int parity, int64_t *n,
+                                   double *d, double *e);
+
+/*
+ * Launch accounting, for benchmarks (not part of the method).
+ * fst_launch_count   -- number of kernels this process has launched through the
+ *                       library so far (plan-time and apply kernels).
+ * fst_profile_enable -- on != 0: from now on, every apply-kernel launch is
+ *                       bracketed by CUDA events on its stream; clears earlier
+ *                       records.  on == 0 stops recording (and clears).
+ * fst_profile_count  -- number of recorded launches.
+ * fst_profile_read   -- record i: kernel name (static string), elapsed device time
+ *                       in ms between its events (waits for them), and the number
+ *                       of signal pairs it processed.  FST_EINVAL if i is out of range.
+ */
+long long fst_launch_count(void);
+fst_status fst_profile_enable(int on);
+int fst_profile_count(void);
+fst_status fst_profile_read(int i, const char **name, double *ms, long long *units);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FST_GB300_H */

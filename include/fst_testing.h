@@ -1,0 +1,30 @@
+/*
+ * fst_testing.h -- host-emulation entry points of libfst_gb300.so, for CPU tests.
+ *
+ * A plan made by fst_emu_plan_op runs every kernel body of the library on the host
+ * (one thread block at a time, the threads of a block looped between barriers),
+ * with all buffers in host memory.  Every other entry point of fst.h accepts such
+ * a plan; its signal pointers are then HOST pointers and `stream` is ignored.
+ * This checks the library's index arithmetic and plan logic without a GPU; it is
+ * slow and not meant for production use.
+ */
+#ifndef FST_GB300_TESTING_H
+#define FST_GB300_TESTING_H
+
+#include "fst.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* as fst_plan_op, executed by the host emulator.  Same argument rules and errors. */
+fst_status fst_emu_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op, double alpha);
+
+/* 1 if the plan runs on the host emulator, 0 otherwise (including NULL). */
+int fst_plan_is_emulated(fst_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FST_GB300_TESTING_H */

@@ -1,0 +1,475 @@
+// fst_device.cu -- CUDA back-end of the fast Slepian projection library (sm_103a):
+// the __global__ wrappers of the kernel bodies, the device Runner, and the
+// host-buffer entry point with overlapped copies.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fst_internal.h"
+
+namespace fst {
+
+template <typename T> struct DevEx {
+  using State = KState<T>;
+  int nthr;
+  int tid;
+  State st;
+  __device__ DevEx() : nthr(blockDim.x), tid(threadIdx.x) {}
+  template <typename F> __device__ __forceinline__ void phase(F &&f) {
+    f(tid, st);
+    __syncthreads();
+  }
+};
+
+struct NoState {
+  c2<double> v[1];
+};
+struct DevExPlan {
+  using State = NoState;
+  int nthr;
+  int tid;
+  State st;
+  __device__ DevExPlan() : nthr(blockDim.x), tid(threadIdx.x) {}
+  template <typename F> __device__ __forceinline__ void phase(F &&f) {
+    f(tid, st);
+    __syncthreads();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// apply kernels
+// ---------------------------------------------------------------------------
+
+template <typename T> __global__ void __launch_bounds__(1024) k_small(const ConvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = 1 << a.log2M;
+  c2<T> *buf = reinterpret_cast<c2<T> *>(smem);
+  T *red = reinterpret_cast<T *>(smem + padded_size(L) * sizeof(c2<T>));
+  T *coef = red + ((blockDim.x + 31) / 32) * 128;
+  DevEx<T> ex;
+  small_body<T>(ex, a, (int64_t)blockIdx.x, buf, red, coef);
+}
+
+template <typename T> __global__ void __launch_bounds__(1024) k_passA(const ConvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int P = 1 << a.log2P;
+  const int ncols = a.G * a.NB;
+  c2<T> *buf = reinterpret_cast<c2<T> *>(smem);
+  T *red = reinterpret_cast<T *>(smem + padded_size(P * ncols) * sizeof(c2<T>));
+  DevEx<T> ex;
+  passA_body<T>(ex, a, (int64_t)blockIdx.x, (int64_t)blockIdx.y, buf, red);
+}
+
+template <typename T> __global__ void k_reduce(const ConvArgs<T> a) {
+  reduce_body<T>(a, (int64_t)blockIdx.x, threadIdx.x, blockDim.x);
+}
+
+template <typename T> __global__ void __launch_bounds__(1024) k_passB(const ConvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  c2<T> *buf = reinterpret_cast<c2<T> *>(smem);
+  DevEx<T> ex;
+  passB_body<T>(ex, a, (int64_t)blockIdx.y, (int)blockIdx.x, buf);
+}
+
+template <typename T> __global__ void __launch_bounds__(1024) k_passC(const ConvArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  c2<T> *buf = reinterpret_cast<c2<T> *>(smem);
+  DevEx<T> ex;
+  passC_body<T>(ex, a, (int64_t)blockIdx.x, (int64_t)blockIdx.y, buf);
+}
+
+// ---------------------------------------------------------------------------
+// plan kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_bisect(const double *d, const double *e2, int n, const int *targets, double glo, double ghi,
+                         double pivmin, double *out, int *flag) {
+  __shared__ BisectShared sh;
+  DevExPlan ex;
+  bisect_body(ex, d, e2, n, targets[blockIdx.x], glo, ghi, pivmin, out + blockIdx.x, flag, &sh);
+}
+
+__global__ void k_invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
+                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  invit_body(d, e, n, sigma[t], tol, iters, t, nt, x, fd, fdl, fdu, fdu2, piv);
+}
+
+__global__ void k_finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) {
+  __shared__ double sh[2 * 256];
+  DevExPlan ex;
+  finalize_body(ex, x, n, nt, (int)blockIdx.x, parity, N, S + (int64_t)blockIdx.x * N, sh);
+}
+
+__global__ void k_dot(const double *a, const double *b, int64_t N, double *out) {
+  __shared__ double sh[256];
+  DevExPlan ex;
+  const int64_t off = (int64_t)blockIdx.x * N;
+  dot_body(ex, a + off, b + off, N, out + blockIdx.x, sh);
+}
+
+__global__ void k_sinc(double *c, int64_t N, int64_t M, double W) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x)
+    c[k] = sinc_embed_at(k, N, M, W);
+}
+
+__global__ void k_spec_store(const double2 *X, Layout L64, Layout L32, int64_t M, double scale, double *spec64,
+                             float *spec32) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p64 = spec_pos(L64, k);
+    const double v = X[p64].x * scale;
+    spec64[p64] = v;
+    spec32[spec_pos(L32, k)] = (float)v;
+  }
+}
+
+__global__ void k_gather(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64, float *ST32) {
+  const int64_t total = N * rpad;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t / rpad;
+    const int j = (int)(t % rpad);
+    const double v = (j < r) ? S[(int64_t)sel[j] * N + n] : 0.0;
+    ST64[t] = v;
+    ST32[t] = (float)v;
+  }
+}
+
+__global__ void k_to_f32(const double *src, float *dst, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = (float)src[t];
+}
+
+// ---------------------------------------------------------------------------
+// device runner
+// ---------------------------------------------------------------------------
+
+static fst_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? FST_ENOMEM : FST_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CU(call, what)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, what);  \
+  } while (0)
+#define LAUNCHED(what) CU(cudaGetLastError(), what)
+
+static bool g_attr_done = false;
+static fst_status set_attrs() {
+  if (g_attr_done) return FST_OK;
+  const int mx = 227 * 1024;
+  CU(cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passA<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passA<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passB<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passB<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passC<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_passC<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  g_attr_done = true;
+  return FST_OK;
+}
+
+// ---- launch accounting (fst_launch_count / fst_profile_*) --------------------
+static long long g_launches = 0;
+static int g_prof_on = 0;
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+  long long units;
+};
+static std::vector<ProfRec> g_prof;
+static void prof_begin(cudaStream_t s, const char *name, long long units, cudaEvent_t *ea) {
+  ++g_launches;
+  *ea = nullptr;
+  if (!g_prof_on) return;
+  cudaEventCreate(ea);
+  cudaEventRecord(*ea, s);
+  ProfRec r{name, *ea, nullptr, units};
+  g_prof.push_back(r);
+}
+static void prof_end(cudaStream_t s, cudaEvent_t ea) {
+  if (!g_prof_on || !ea) return;
+  cudaEvent_t eb;
+  cudaEventCreate(&eb);
+  cudaEventRecord(eb, s);
+  g_prof.back().b = eb;
+}
+#define PROF(name, units, launch)            \
+  do {                                       \
+    cudaEvent_t _ea;                         \
+    prof_begin(s, name, (units), &_ea);      \
+    launch;                                  \
+    prof_end(s, _ea);                        \
+  } while (0)
+
+static inline int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+struct DevRunner : Runner {
+  cudaStream_t s = nullptr;
+  bool device() const override { return true; }
+  void set_stream(void *st) override { s = (cudaStream_t)st; }
+  void *stream() const override { return (void *)s; }
+
+  fst_status alloc(void **p, size_t bytes) override {
+    *p = nullptr;
+    CU(cudaMalloc(p, std::max<size_t>(bytes, 16)), "cudaMalloc");
+    return FST_OK;
+  }
+  void release(void *p) override {
+    if (p) cudaFree(p);
+  }
+  fst_status h2d(void *dst, const void *src, size_t bytes) override {
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), "h2d");
+    CU(cudaStreamSynchronize(s), "h2d sync");
+    return FST_OK;
+  }
+  fst_status d2h(void *dst, const void *src, size_t bytes) override {
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "d2h");
+    CU(cudaStreamSynchronize(s), "d2h sync");
+    return FST_OK;
+  }
+  fst_status d2d(void *dst, const void *src, size_t bytes) override {
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s), "d2d");
+    return FST_OK;
+  }
+  fst_status zero(void *p, size_t bytes) override {
+    CU(cudaMemsetAsync(p, 0, bytes, s), "memset");
+    return FST_OK;
+  }
+  fst_status sync() override {
+    CU(cudaStreamSynchronize(s), "sync");
+    return FST_OK;
+  }
+
+  template <typename T> fst_status small_t(const ConvArgs<T> &a, const Layout &L) {
+    if (set_attrs() != FST_OK) return FST_ECUDA;
+    PROF(sizeof(T) == 4 ? "k_small<f32>" : "k_small<f64>", a.npairs,
+         (k_small<T><<<(unsigned)a.npairs, L.nthr_small, L.smem_small, s>>>(a)));
+    LAUNCHED("k_small");
+    return FST_OK;
+  }
+  template <typename T> fst_status passA_t(const ConvArgs<T> &a, const Layout &L) {
+    if (set_attrs() != FST_OK) return FST_ECUDA;
+    dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + L.G - 1) / L.G));
+    PROF(sizeof(T) == 4 ? "k_passA<f32>" : "k_passA<f64>", a.npairs, (k_passA<T><<<grid, L.nthr_A, L.smem_A, s>>>(a)));
+    LAUNCHED("k_passA");
+    return FST_OK;
+  }
+  template <typename T> fst_status reduce_t(const ConvArgs<T> &a, const Layout &) {
+    const int thr = std::min(1024, std::max(32, ((2 * a.r + 31) / 32) * 32));
+    PROF(sizeof(T) == 4 ? "k_reduce<f32>" : "k_reduce<f64>", a.npairs, (k_reduce<T><<<(unsigned)a.npairs, thr, 0, s>>>(a)));
+    LAUNCHED("k_reduce");
+    return FST_OK;
+  }
+  template <typename T> fst_status passB_t(const ConvArgs<T> &a, const Layout &L) {
+    if (set_attrs() != FST_OK) return FST_ECUDA;
+    dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
+    PROF(sizeof(T) == 4 ? "k_passB<f32>" : "k_passB<f64>", a.npairs, (k_passB<T><<<grid, L.nthr_B, L.smem_B, s>>>(a)));
+    LAUNCHED("k_passB");
+    return FST_OK;
+  }
+  template <typename T> fst_status passC_t(const ConvArgs<T> &a, const Layout &L) {
+    if (set_attrs() != FST_OK) return FST_ECUDA;
+    dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + L.G - 1) / L.G));
+    PROF(sizeof(T) == 4 ? "k_passC<f32>" : "k_passC<f64>", a.npairs, (k_passC<T><<<grid, L.nthr_C, L.smem_C, s>>>(a)));
+    LAUNCHED("k_passC");
+    return FST_OK;
+  }
+  fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
+  fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
+  fst_status passA(const ConvArgs<float> &a, const Layout &L) override { return passA_t(a, L); }
+  fst_status passA(const ConvArgs<double> &a, const Layout &L) override { return passA_t(a, L); }
+  fst_status reduce(const ConvArgs<float> &a, const Layout &L) override { return reduce_t(a, L); }
+  fst_status reduce(const ConvArgs<double> &a, const Layout &L) override { return reduce_t(a, L); }
+  fst_status passB(const ConvArgs<float> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status passC(const ConvArgs<float> &a, const Layout &L) override { return passC_t(a, L); }
+  fst_status passC(const ConvArgs<double> &a, const Layout &L) override { return passC_t(a, L); }
+
+  fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
+                    double pivmin, double *out, int *flag) override {
+    k_bisect<<<nt, BISECT_THREADS, 0, s>>>(d, e2, n, targets, glo, ghi, pivmin, out, flag);
+    LAUNCHED("k_bisect");
+    return FST_OK;
+  }
+  fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
+                   double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
+    k_invit<<<(nt + 31) / 32, 32, 0, s>>>(d, e, n, sigma, nt, tol, iters, x, fd, fdl, fdu, fdu2, piv);
+    LAUNCHED("k_invit");
+    return FST_OK;
+  }
+  fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
+    k_finalize<<<nt, 256, 0, s>>>(x, n, nt, parity, N, S);
+    LAUNCHED("k_finalize");
+    return FST_OK;
+  }
+  fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) override {
+    k_dot<<<nvec, 256, 0, s>>>(a, b, N, out);
+    LAUNCHED("k_dot");
+    return FST_OK;
+  }
+  fst_status sinc_embed(double *c, int64_t N, int64_t M, double W) override {
+    k_sinc<<<grid_for(M, 256), 256, 0, s>>>(c, N, M, W);
+    LAUNCHED("k_sinc");
+    return FST_OK;
+  }
+  fst_status spec_store(const double2 *X, const Layout &L64, const Layout &L32, int64_t M, double scale,
+                        double *spec64, float *spec32) override {
+    k_spec_store<<<grid_for(M, 256), 256, 0, s>>>(X, L64, L32, M, scale, spec64, spec32);
+    LAUNCHED("k_spec_store");
+    return FST_OK;
+  }
+  fst_status gather_ST(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64,
+                       float *ST32) override {
+    k_gather<<<grid_for(N * rpad, 256), 256, 0, s>>>(S, N, sel, r, rpad, ST64, ST32);
+    LAUNCHED("k_gather");
+    return FST_OK;
+  }
+  fst_status to_f32(const double *src, float *dst, int64_t n) override {
+    k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+    LAUNCHED("k_to_f32");
+    return FST_OK;
+  }
+};
+
+Runner *make_dev_runner() {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return new DevRunner();
+}
+
+}  // namespace fst
+
+using namespace fst;
+
+extern "C" long long fst_launch_count(void) { return g_launches; }
+
+extern "C" fst_status fst_profile_enable(int on) {
+  for (auto &r : g_prof) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = on ? 1 : 0;
+  return FST_OK;
+}
+
+extern "C" fst_status fst_profile_read(int i, const char **name, double *ms, long long *units) {
+  if (i < 0 || i >= (int)g_prof.size()) return fail(FST_EINVAL, "profile index out of range");
+  ProfRec &r = g_prof[i];
+  float t = 0.f;
+  if (r.a && r.b) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "event sync");
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "elapsed");
+  }
+  if (name) *name = r.name;
+  if (ms) *ms = t;
+  if (units) *units = r.units;
+  return FST_OK;
+}
+
+extern "C" int fst_profile_count(void) { return (int)g_prof.size(); }
+
+// ---------------------------------------------------------------------------
+// host-buffer entry point: chunks of the batch go host -> device -> host on two
+// copy streams while the previous / next chunk is projected on `stream`
+// ---------------------------------------------------------------------------
+namespace {
+struct HostPipe {
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+  void *din[2] = {}, *dout[2] = {};
+  size_t slot_bytes = 0;
+  int dev = -1;
+};
+thread_local HostPipe *g_pipe = nullptr;
+}  // namespace
+
+extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, int64_t batch, int dtype,
+                                       void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FST_EINVAL, "batch < 0");
+  if (batch == 0) return FST_OK;
+  if (!y || !out) return fail(FST_EINVAL, "NULL signal pointer");
+  if (!p->R->device()) return run_apply(p, y, out, batch, 0, dtype, true);
+  size_t esz;
+  switch (dtype) {
+    case FST_F32: esz = 4; break;
+    case FST_F64: esz = 8; break;
+    case FST_C64: esz = 8; break;
+    case FST_C128: esz = 16; break;
+    default: return fail(FST_EINVAL, "unknown dtype");
+  }
+  const size_t sig_bytes = esz * (size_t)p->N;
+  int64_t per = std::max<int64_t>(2, (int64_t)((64u << 20) / sig_bytes));
+  per = (per / 2) * 2;
+  per = std::min<int64_t>(per, ((batch + 1) / 2) * 2);
+  const size_t slot = (size_t)per * sig_bytes;
+  int dev = 0;
+  CU(cudaGetDevice(&dev), "cudaGetDevice");
+  if (!g_pipe || g_pipe->dev != dev || g_pipe->slot_bytes < slot) {
+    if (g_pipe) {
+      for (int i = 0; i < 2; ++i) {
+        cudaFree(g_pipe->din[i]);
+        cudaFree(g_pipe->dout[i]);
+      }
+    } else {
+      g_pipe = new HostPipe();
+    }
+    if (!g_pipe->cin) {
+      CU(cudaStreamCreateWithFlags(&g_pipe->cin, cudaStreamNonBlocking), "stream");
+      CU(cudaStreamCreateWithFlags(&g_pipe->cout, cudaStreamNonBlocking), "stream");
+      for (int i = 0; i < 2; ++i) {
+        CU(cudaEventCreateWithFlags(&g_pipe->in_done[i], cudaEventDisableTiming), "event");
+        CU(cudaEventCreateWithFlags(&g_pipe->comp_done[i], cudaEventDisableTiming), "event");
+        CU(cudaEventCreateWithFlags(&g_pipe->out_done[i], cudaEventDisableTiming), "event");
+      }
+    }
+    for (int i = 0; i < 2; ++i) {
+      g_pipe->din[i] = g_pipe->dout[i] = nullptr;
+      CU(cudaMalloc(&g_pipe->din[i], slot), "cudaMalloc");
+      CU(cudaMalloc(&g_pipe->dout[i], slot), "cudaMalloc");
+    }
+    g_pipe->slot_bytes = slot;
+    g_pipe->dev = dev;
+  }
+  HostPipe &hp = *g_pipe;
+  cudaStream_t sc = (cudaStream_t)stream;
+  p->R->set_stream(stream);
+  // the copies must not start before earlier work on the compute stream is done
+  CU(cudaEventRecord(hp.comp_done[0], sc), "event");
+  CU(cudaStreamWaitEvent(hp.cin, hp.comp_done[0], 0), "wait");
+  int64_t i = 0;
+  for (int64_t b0 = 0; b0 < batch; b0 += per, ++i) {
+    const int k = (int)(i & 1);
+    const int64_t nb = std::min<int64_t>(per, batch - b0);
+    const size_t bytes = (size_t)nb * sig_bytes;
+    if (i >= 2) CU(cudaStreamWaitEvent(hp.cin, hp.out_done[k], 0), "wait");
+    CU(cudaMemcpyAsync(hp.din[k], (const char *)y + b0 * sig_bytes, bytes, cudaMemcpyHostToDevice, hp.cin), "h2d");
+    CU(cudaEventRecord(hp.in_done[k], hp.cin), "event");
+    CU(cudaStreamWaitEvent(sc, hp.in_done[k], 0), "wait");
+    fst_status s = run_apply(p, hp.din[k], hp.dout[k], nb, 0, dtype, true);
+    if (s != FST_OK) return s;
+    CU(cudaEventRecord(hp.comp_done[k], sc), "event");
+    CU(cudaStreamWaitEvent(hp.cout, hp.comp_done[k], 0), "wait");
+    CU(cudaMemcpyAsync((char *)out + b0 * sig_bytes, hp.dout[k], bytes, cudaMemcpyDeviceToHost, hp.cout), "d2h");
+    CU(cudaEventRecord(hp.out_done[k], hp.cout), "event");
+  }
+  CU(cudaStreamSynchronize(hp.cout), "sync");
+  CU(cudaStreamSynchronize(sc), "sync");
+  return FST_OK;
+}

@@ -1,0 +1,168 @@
+// fst_emu.cu -- host emulation back-end: runs the library's kernel bodies on the
+// CPU, one thread block at a time, with the block's threads looped inside each
+// phase (a phase ends where the device kernel has a __syncthreads()).  Buffers live
+// in host memory.  Used by the CPU test-suite to check index arithmetic, layouts
+// and the plan logic without a GPU.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fst_internal.h"
+
+namespace fst {
+
+template <typename S> struct HostEx {
+  using State = S;
+  int nthr;
+  std::vector<State> st;
+  explicit HostEx(int n) : nthr(n), st(n) {}
+  template <typename F> void phase(F &&f) {
+    for (int t = 0; t < nthr; ++t) f(t, st[t]);
+  }
+};
+struct NoStateH {
+  c2<double> v[1];
+};
+
+struct EmuRunner : Runner {
+  bool device() const override { return false; }
+  fst_status alloc(void **p, size_t bytes) override {
+    *p = calloc(1, std::max<size_t>(bytes, 16));
+    if (!*p) return fail(FST_ENOMEM, "host allocation failed");
+    return FST_OK;
+  }
+  void release(void *p) override { free(p); }
+  fst_status h2d(void *dst, const void *src, size_t bytes) override { memcpy(dst, src, bytes); return FST_OK; }
+  fst_status d2h(void *dst, const void *src, size_t bytes) override { memcpy(dst, src, bytes); return FST_OK; }
+  fst_status d2d(void *dst, const void *src, size_t bytes) override { memmove(dst, src, bytes); return FST_OK; }
+  fst_status zero(void *p, size_t bytes) override { memset(p, 0, bytes); return FST_OK; }
+  fst_status sync() override { return FST_OK; }
+
+  template <typename T> fst_status small_t(const ConvArgs<T> &a, const Layout &L) {
+    std::vector<unsigned char> smem(L.smem_small + 64);
+    const int Lsz = 1 << a.log2M;
+    c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
+    T *red = reinterpret_cast<T *>(smem.data() + padded_size(Lsz) * sizeof(c2<T>));
+    T *coef = red + ((L.nthr_small + 31) / 32) * 128;
+    for (int64_t pl = 0; pl < a.npairs; ++pl) {
+      HostEx<KState<T>> ex(L.nthr_small);
+      small_body<T>(ex, a, pl, buf, red, coef);
+    }
+    return FST_OK;
+  }
+  template <typename T> fst_status passA_t(const ConvArgs<T> &a, const Layout &L) {
+    std::vector<unsigned char> smem(L.smem_A + 64);
+    const int P = 1 << a.log2P;
+    c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
+    T *red = reinterpret_cast<T *>(smem.data() + padded_size(P * a.G * a.NB) * sizeof(c2<T>));
+    const int64_t ngroups = (a.npairs + L.G - 1) / L.G;
+    for (int64_t g = 0; g < ngroups; ++g)
+      for (int64_t t = 0; t < L.ntiles; ++t) {
+        HostEx<KState<T>> ex(L.nthr_A);
+        passA_body<T>(ex, a, t, g, buf, red);
+      }
+    return FST_OK;
+  }
+  template <typename T> fst_status reduce_t(const ConvArgs<T> &a, const Layout &) {
+    for (int64_t pl = 0; pl < a.npairs; ++pl)
+      for (int t = 0; t < 64; ++t) reduce_body<T>(a, pl, t, 64);
+    return FST_OK;
+  }
+  template <typename T> fst_status passB_t(const ConvArgs<T> &a, const Layout &L) {
+    std::vector<unsigned char> smem(L.smem_B + 64);
+    c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
+    for (int64_t pl = 0; pl < a.npairs; ++pl)
+      for (int k1 = 0; k1 < (1 << L.log2P); ++k1) {
+        HostEx<KState<T>> ex(L.nthr_B);
+        passB_body<T>(ex, a, pl, k1, buf);
+      }
+    return FST_OK;
+  }
+  template <typename T> fst_status passC_t(const ConvArgs<T> &a, const Layout &L) {
+    std::vector<unsigned char> smem(L.smem_C + 64);
+    c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
+    const int64_t ngroups = (a.npairs + L.G - 1) / L.G;
+    for (int64_t g = 0; g < ngroups; ++g)
+      for (int64_t t = 0; t < L.ntiles; ++t) {
+        HostEx<KState<T>> ex(L.nthr_C);
+        passC_body<T>(ex, a, t, g, buf);
+      }
+    return FST_OK;
+  }
+  fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
+  fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
+  fst_status passA(const ConvArgs<float> &a, const Layout &L) override { return passA_t(a, L); }
+  fst_status passA(const ConvArgs<double> &a, const Layout &L) override { return passA_t(a, L); }
+  fst_status reduce(const ConvArgs<float> &a, const Layout &L) override { return reduce_t(a, L); }
+  fst_status reduce(const ConvArgs<double> &a, const Layout &L) override { return reduce_t(a, L); }
+  fst_status passB(const ConvArgs<float> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status passC(const ConvArgs<float> &a, const Layout &L) override { return passC_t(a, L); }
+  fst_status passC(const ConvArgs<double> &a, const Layout &L) override { return passC_t(a, L); }
+
+  fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
+                    double pivmin, double *out, int *flag) override {
+    for (int t = 0; t < nt; ++t) {
+      BisectShared sh;
+      HostEx<NoStateH> ex(BISECT_THREADS);
+      bisect_body(ex, d, e2, n, targets[t], glo, ghi, pivmin, out + t, flag, &sh);
+    }
+    return FST_OK;
+  }
+  fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
+                   double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
+    for (int t = 0; t < nt; ++t) invit_body(d, e, n, sigma[t], tol, iters, t, nt, x, fd, fdl, fdu, fdu2, piv);
+    return FST_OK;
+  }
+  fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
+    std::vector<double> sh(2 * 256);
+    for (int t = 0; t < nt; ++t) {
+      HostEx<NoStateH> ex(256);
+      finalize_body(ex, x, n, nt, t, parity, N, S + (int64_t)t * N, sh.data());
+    }
+    return FST_OK;
+  }
+  fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) override {
+    std::vector<double> sh(256);
+    for (int v = 0; v < nvec; ++v) {
+      HostEx<NoStateH> ex(256);
+      dot_body(ex, a + (int64_t)v * N, b + (int64_t)v * N, N, out + v, sh.data());
+    }
+    return FST_OK;
+  }
+  fst_status sinc_embed(double *c, int64_t N, int64_t M, double W) override {
+    for (int64_t k = 0; k < M; ++k) c[k] = sinc_embed_at(k, N, M, W);
+    return FST_OK;
+  }
+  fst_status spec_store(const double2 *X, const Layout &L64, const Layout &L32, int64_t M, double scale,
+                        double *spec64, float *spec32) override {
+    for (int64_t k = 0; k < M; ++k) {
+      const int64_t p64 = spec_pos(L64, k);
+      const double v = X[p64].x * scale;
+      spec64[p64] = v;
+      spec32[spec_pos(L32, k)] = (float)v;
+    }
+    return FST_OK;
+  }
+  fst_status gather_ST(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64,
+                       float *ST32) override {
+    for (int64_t n = 0; n < N; ++n)
+      for (int j = 0; j < rpad; ++j) {
+        const double v = (j < r) ? S[(int64_t)sel[j] * N + n] : 0.0;
+        ST64[n * rpad + j] = v;
+        ST32[n * rpad + j] = (float)v;
+      }
+    return FST_OK;
+  }
+  fst_status to_f32(const double *src, float *dst, int64_t n) override {
+    for (int64_t i = 0; i < n; ++i) dst[i] = (float)src[i];
+    return FST_OK;
+  }
+};
+
+Runner *make_emu_runner() { return new EmuRunner(); }
+
+}  // namespace fst

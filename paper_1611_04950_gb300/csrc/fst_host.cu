@@ -1,0 +1,660 @@
+// fst_host.cu -- plan construction, launch sequencing and the C ABI of the fast
+// Slepian projection library.  Written against the abstract Runner, so the same
+// code drives the GPU (DevRunner) and the host emulator (EmuRunner).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fst_internal.h"
+#include "../../include/fst_testing.h"
+
+namespace fst {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+fst_status fail(fst_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+#define TRY(expr)                         \
+  do {                                    \
+    fst_status _s = (expr);               \
+    if (_s != FST_OK) return _s;          \
+  } while (0)
+
+static int ilog2_exact(int64_t x) {
+  int l = 0;
+  while ((1LL << l) < x) ++l;
+  return l;
+}
+
+// ---------------------------------------------------------------------------
+// layouts
+// ---------------------------------------------------------------------------
+
+static int64_t chunk_bytes_target() {
+  const char *s = getenv("FST_CHUNK_MB");
+  int64_t mb = s ? atoll(s) : 64;
+  if (mb < 1) mb = 1;
+  return mb << 20;
+}
+
+Layout make_layout(int64_t N, int log2M, bool dbl, int rpad) {
+  Layout L;
+  const size_t cs = dbl ? 16 : 8;   // bytes per complex
+  const size_t rs = dbl ? 8 : 4;    // bytes per real
+  L.log2M = log2M;
+  const int small_max = dbl ? 13 : 14;
+  const int64_t M = 1LL << log2M;
+  if (log2M <= small_max) {
+    L.small = true;
+    const int Lsz = 1 << log2M;
+    int nthr = Lsz / 16;
+    nthr = std::max(64, std::min(1024, nthr));
+    L.nthr_small = nthr;
+    const int nwarps = (nthr + 31) / 32;
+    L.smem_small = padded_size(Lsz) * cs + (size_t)nwarps * 128 * rs + 2 * (size_t)std::max(rpad, 1) * rs;
+    L.chunk = std::max<int64_t>(1, chunk_bytes_target() / (int64_t)(M * cs));
+    return L;
+  }
+  L.small = false;
+  const int qmax = dbl ? 13 : 14, qmin = dbl ? 11 : 12;
+  L.log2Q = std::min(qmax, std::max(qmin, log2M - 5));
+  L.log2P = log2M - L.log2Q;
+  const int P = 1 << L.log2P, Q = 1 << L.log2Q;
+  const int tile = 8192;
+  const int ncols = std::max(1, tile / P);
+  const int nb0 = std::min(32, ncols);
+  L.G = std::min(ncols / nb0, 16);
+  L.NB = ncols / L.G;
+  L.ntiles = Q / L.NB;
+  L.Pnz = (int)((N + Q - 1) / Q);
+  L.nthr_A = L.nthr_C = std::max(32, ncols * P / 16);
+  L.nthr_B = std::max(32, Q / 16);
+  const int nwarps = L.nthr_A / 32;
+  L.smem_A = padded_size(P * ncols) * cs + (size_t)nwarps * 128 * rs;
+  L.smem_C = padded_size(P * ncols) * cs;
+  L.smem_B = padded_size(Q) * cs;
+  int64_t ch = chunk_bytes_target() / (int64_t)(M * cs);
+  ch = std::max<int64_t>(L.G, (ch / L.G) * L.G);
+  L.chunk = ch;
+  return L;
+}
+
+static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
+  const size_t cs = dbl ? 16 : 8, rs = dbl ? 8 : 4;
+  const int64_t M = 1LL << L.log2M;
+  if (L.small) return forward ? (size_t)L.chunk * M * cs : 0;
+  size_t b = (size_t)L.chunk * M * cs;
+  b += (size_t)L.chunk * L.ntiles * 2 * std::max(rpad, 1) * rs;
+  b += (size_t)L.chunk * 2 * std::max(rpad, 1) * rs;
+  return b + 1024;
+}
+
+// ---------------------------------------------------------------------------
+// convolution driver
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t npairs, void *ws) {
+  using C = c2<T>;
+  a.log2M = L.log2M;
+  a.log2P = L.log2P;
+  a.log2Q = L.log2Q;
+  a.Pnz = L.Pnz;
+  a.NB = L.NB;
+  a.G = L.G;
+  if (a.mode == MODE_FORWARD && !L.small) a.Pnz = 1 << L.log2P;
+  const int64_t M = 1LL << L.log2M;
+  char *w = (char *)ws;
+  a.inter = (C *)w;
+  if (!L.small) {
+    const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
+    a.part = (T *)(w + inter_b);
+    a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
+  }
+  for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk) {
+    a.pair0 = p0;
+    a.npairs = std::min<int64_t>(L.chunk, npairs - p0);
+    if (L.small) {
+      TRY(R->small(a, L));
+    } else {
+      TRY(R->passA(a, L));
+      if (a.mode == MODE_FULL && a.r > 0) TRY(R->reduce(a, L));
+      TRY(R->passB(a, L));
+      if (a.mode != MODE_FORWARD) TRY(R->passC(a, L));
+    }
+  }
+  return FST_OK;
+}
+
+template <typename T> static Tw<T> plan_tw(fst_plan_t p);
+template <> Tw<float> plan_tw<float>(fst_plan_t p) { return Tw<float>{p->tw32h, p->tw32l}; }
+template <> Tw<double> plan_tw<double>(fst_plan_t p) { return Tw<double>{p->tw64h, p->tw64l}; }
+
+static fst_status ensure_ws(fst_plan_t p, size_t bytes) {
+  if (bytes <= p->ws_bytes) return FST_OK;
+  if (p->ws) p->R->release(p->ws);
+  p->ws = nullptr;
+  p->ws_bytes = 0;
+  TRY(p->R->alloc(&p->ws, bytes));
+  p->ws_bytes = bytes;
+  return FST_OK;
+}
+
+template <typename T>
+static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64_t ld, bool cplx, bool full,
+                          const T *spec, const T *ST, const T *D, const Layout &L) {
+  ConvArgs<T> a{};
+  a.y = y;
+  a.out = out;
+  a.ld = ld;
+  a.batch = batch;
+  a.cplx = cplx ? 1 : 0;
+  a.N = p->N;
+  a.spec = spec;
+  a.ST = ST;
+  a.r = full ? (int)p->r : 0;
+  a.rpad = (int)p->rpad;
+  a.D = D;
+  a.tw = plan_tw<T>(p);
+  a.mode = full ? MODE_FULL : MODE_CONV;
+  const int64_t npairs = cplx ? batch : (batch + 1) / 2;
+  TRY(ensure_ws(p, ws_need(L, sizeof(T) == 8, (int)p->rpad, false)));
+  return run_conv<T>(p->R, L, a, npairs, p->ws);
+}
+
+fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FST_EINVAL, "batch < 0");
+  if (batch == 0) return FST_OK;
+  if (!y || !out) return fail(FST_EINVAL, "NULL signal pointer");
+  if (ld == 0) ld = p->N;
+  if (ld < p->N) return fail(FST_EINVAL, "ld < N");
+  switch (dtype) {
+    case FST_F32:
+      return apply_t<float>(p, (const float *)y, (float *)out, batch, ld, false, full, p->spec32, p->ST32, p->D32,
+                            p->lay32);
+    case FST_C64:
+      return apply_t<float>(p, (const float *)y, (float *)out, batch, ld, true, full, p->spec32, p->ST32, p->D32,
+                            p->lay32);
+    case FST_F64:
+      return apply_t<double>(p, (const double *)y, (double *)out, batch, ld, false, full, p->spec64, p->ST64,
+                             p->D64, p->lay64);
+    case FST_C128:
+      return apply_t<double>(p, (const double *)y, (double *)out, batch, ld, true, full, p->spec64, p->ST64,
+                             p->D64, p->lay64);
+    default:
+      return fail(FST_EINVAL, "unknown dtype");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+
+static double cospi_host(double x) {
+  // cos(pi x) for x in [0, 1] with exact zero at 1/2 (the differences are exact)
+  if (x <= 0.25) return cos(M_PI * x);
+  if (x <= 0.75) return sin(M_PI * (0.5 - x));
+  return -cos(M_PI * (1.0 - x));
+}
+
+struct Reduced {
+  int n = 0;
+  std::vector<double> d, e, e2;  // e[i] couples i-1 and i (e[0] = 0)
+};
+
+static Reduced reduced_tridiagonal(int64_t N, double W, int parity) {
+  Reduced R;
+  const double cw = cospi_host(2.0 * W);
+  auto dfull = [&](int64_t i) {
+    const double c = 0.5 * (double)(N - 1) - (double)i;
+    return c * c * cw;
+  };
+  auto efull = [&](int64_t i) { return 0.5 * (double)i * (double)(N - i); };
+  const int64_t m = N / 2;
+  const bool odd = (N & 1) != 0;
+  int64_t n;
+  if (!odd) n = m;
+  else n = (parity == 0) ? m + 1 : m;
+  R.n = (int)n;
+  R.d.resize(n);
+  R.e.assign(n, 0.0);
+  R.e2.assign(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) R.d[i] = dfull(i);
+  for (int64_t i = 1; i < n; ++i) R.e[i] = efull(i);
+  if (!odd && n > 0) R.d[n - 1] += (parity == 0 ? 1.0 : -1.0) * efull(m);
+  if (odd && parity == 0 && n > 1) R.e[n - 1] = sqrt(2.0) * efull(m);
+  for (int64_t i = 1; i < n; ++i) R.e2[i] = R.e[i] * R.e[i];
+  return R;
+}
+
+static void build_twiddles(std::vector<double2> &hi, std::vector<double2> &lo) {
+  hi.resize(TW_HI_SIZE);
+  lo.resize(TW_LO_SIZE);
+  // exp(-2 pi i k / 2^24); the angle fraction k / 2^24 is exact in double
+  for (int a = 0; a < TW_HI_SIZE; ++a) {
+    const double f = (double)((int64_t)a << TW_SPLIT) / (double)(1 << TW_LOG2);
+    hi[a] = make_double2(cos(2.0 * M_PI * f), -sin(2.0 * M_PI * f));
+  }
+  for (int b = 0; b < TW_LO_SIZE; ++b) {
+    const double f = (double)b / (double)(1 << TW_LOG2);
+    lo[b] = make_double2(cos(2.0 * M_PI * f), -sin(2.0 * M_PI * f));
+  }
+}
+
+static double asymptotic_transition(int64_t N, double eps) {
+  const double n = (double)std::max<int64_t>(N, 2);
+  return 2.0 / (M_PI * M_PI) * log(n) * log(1.0 / eps - 1.0);
+}
+static double cor1_bound(int64_t N, double eps) {
+  return (8.0 / (M_PI * M_PI) * log(8.0 * (double)N) + 12.0) * log(15.0 / eps);
+}
+
+struct Scoped {
+  Runner *R;
+  std::vector<void *> ptrs;
+  explicit Scoped(Runner *r) : R(r) {}
+  ~Scoped() { for (void *q : ptrs) R->release(q); }
+  template <typename P> fst_status alloc(P **p, size_t n) {
+    void *q = nullptr;
+    fst_status s = R->alloc(&q, std::max<size_t>(n, 1) * sizeof(P));
+    if (s != FST_OK) return s;
+    ptrs.push_back(q);
+    *p = (P *)q;
+    return FST_OK;
+  }
+};
+
+static bool in_T(double lam, int64_t l, int64_t K, double eps, int op, double alpha) {
+  if (op == FST_OP_TIKHONOV) return lam > alpha * (1.0 + alpha) * eps && lam < 1.0 - eps / 3.0;
+  const double one = (l < K) ? 1.0 : 0.0;
+  return fabs(one - lam) > eps;
+}
+static double D_of(double lam, int64_t l, int64_t K, int op, double alpha) {
+  if (op == FST_OP_PROJECT) return (l < K) ? 1.0 - lam : -lam;                 // U1 U2^*, Corollary 2
+  if (op == FST_OP_PINV) return (l < K) ? 1.0 / lam - lam : -lam;              // U3 U4^*, Corollary 3
+  return lam / (lam * lam + alpha) - lam / (1.0 + alpha);                      // U5 U5^*, Corollary 4
+}
+
+// Slepian vectors s^(l), lo <= l <= hi, as rows S[l - lo][0..N), and their
+// eigenvalues lambda_l = s^T B s (FP64 FFT convolution with spec64 = DFT_M(c)/M).
+static fst_status window_vectors(fst_plan_t p, Scoped &sc, int64_t lo, int64_t hi, double *S, double *lam_host,
+                                 const double *spec_unit) {
+  Runner *R = p->R;
+  const int64_t N = p->N;
+  const int nwin = (int)(hi - lo + 1);
+  for (int parity = 0; parity < 2; ++parity) {
+    Reduced red = reduced_tridiagonal(N, p->W, parity);
+    std::vector<int> targets;
+    std::vector<int64_t> ls;
+    for (int64_t l = lo; l <= hi; ++l)
+      if ((l & 1) == parity) {
+        targets.push_back(red.n - 1 - (int)(l >> 1));
+        ls.push_back(l);
+      }
+    if (targets.empty()) continue;
+    const int n = red.n, nt = (int)targets.size();
+    double glo = 1e300, ghi = -1e300, tnorm = 0.0, emax2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double el = fabs(red.e[i]), er = (i + 1 < n) ? fabs(red.e[i + 1]) : 0.0;
+      glo = std::min(glo, red.d[i] - el - er);
+      ghi = std::max(ghi, red.d[i] + el + er);
+      tnorm = std::max(tnorm, fabs(red.d[i]) + el + er);
+      emax2 = std::max(emax2, red.e2[i]);
+    }
+    const double pivmin = 2.2250738585072014e-308 * std::max(1.0, emax2);
+    const double widen = 2.220446049250313e-16 * tnorm * 4.0 + 4.0 * pivmin;
+    glo -= widen;
+    ghi += widen;
+    Scoped loc(R);
+    double *dd, *de, *de2, *theta, *x, *fd, *fdl, *fdu, *fdu2, *Sp;
+    int *dt, *flag;
+    uint8_t *piv;
+    TRY(loc.alloc(&dd, n));
+    TRY(loc.alloc(&de, n));
+    TRY(loc.alloc(&de2, n));
+    TRY(loc.alloc(&dt, nt));
+    TRY(loc.alloc(&theta, nt));
+    TRY(loc.alloc(&flag, 1));
+    TRY(R->h2d(dd, red.d.data(), n * sizeof(double)));
+    TRY(R->h2d(de, red.e.data(), n * sizeof(double)));
+    TRY(R->h2d(de2, red.e2.data(), n * sizeof(double)));
+    TRY(R->h2d(dt, targets.data(), nt * sizeof(int)));
+    TRY(R->zero(flag, sizeof(int)));
+    TRY(R->bisect(dd, de2, n, dt, nt, glo, ghi, pivmin, theta, flag));
+    int hflag = 0;
+    TRY(R->d2h(&hflag, flag, sizeof(int)));
+    if (hflag) return fail(FST_ENOCONVERGE, "bisection did not converge");
+    const size_t nn = (size_t)n * nt;
+    TRY(loc.alloc(&x, nn));
+    TRY(loc.alloc(&fd, nn));
+    TRY(loc.alloc(&fdl, nn));
+    TRY(loc.alloc(&fdu, nn));
+    TRY(loc.alloc(&fdu2, nn));
+    TRY(loc.alloc(&piv, nn));
+    TRY(R->invit(dd, de, n, theta, nt, 2.220446049250313e-16 * tnorm, 3, x, fd, fdl, fdu, fdu2, piv));
+    TRY(loc.alloc(&Sp, (size_t)nt * N));
+    TRY(R->finalize(x, n, nt, parity, N, Sp));
+    for (int k = 0; k < nt; ++k)
+      TRY(R->d2d(S + (size_t)(ls[k] - lo) * N, Sp + (size_t)k * N, (size_t)N * sizeof(double)));
+  }
+  // lambda_l = s_l^T (B s_l)
+  double *BS, *lamd;
+  TRY(sc.alloc(&BS, (size_t)nwin * N));
+  TRY(sc.alloc(&lamd, nwin));
+  {
+    ConvArgs<double> a{};
+    a.y = S;
+    a.out = BS;
+    a.ld = N;
+    a.batch = nwin;
+    a.cplx = 0;
+    a.N = N;
+    a.spec = spec_unit;
+    a.r = 0;
+    a.rpad = 0;
+    a.tw = plan_tw<double>(p);
+    a.mode = MODE_CONV;
+    const Layout L = make_layout(N, p->log2M, true, 0);
+    Scoped wsc(R);
+    void *ws = nullptr;
+    const size_t need = ws_need(L, true, 0, false);
+    if (need) {
+      char *w;
+      TRY(wsc.alloc(&w, need));
+      ws = w;
+    }
+    TRY(run_conv<double>(R, L, a, (nwin + 1) / 2, ws));
+  }
+  TRY(R->dot(S, BS, N, nwin, lamd));
+  TRY(R->d2h(lam_host, lamd, nwin * sizeof(double)));
+  return FST_OK;
+}
+
+fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                      double alpha) {
+  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
+  *out = nullptr;
+  if (!(N >= 1 && N <= (1LL << 23))) { delete R; return fail(FST_EINVAL, "need 1 <= N <= 2^23"); }
+  if (!(W > 0.0 && W < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < W < 1/2"); }
+  if (!(eps > 0.0 && eps < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < eps < 1/2"); }
+  if (op < 0 || op > 2) { delete R; return fail(FST_EINVAL, "unknown operator"); }
+  if (op == FST_OP_TIKHONOV && !(alpha > 0.0)) { delete R; return fail(FST_EINVAL, "Tikhonov needs alpha > 0"); }
+  const int64_t Kdef = (int64_t)floor(2.0 * (double)N * W + 0.5);
+  if (K < 0) K = Kdef;
+  if (K > N) { delete R; return fail(FST_EINVAL, "need 0 <= K <= N"); }
+
+  fst_plan_t p = new fst_plan_s();
+  p->R = R;
+  p->N = N;
+  p->W = W;
+  p->K = K;
+  p->eps = eps;
+  p->op = op;
+  p->alpha = (op == FST_OP_TIKHONOV) ? alpha : 0.0;
+  p->beta = (op == FST_OP_TIKHONOV) ? 1.0 / (1.0 + alpha) : 1.0;
+  int64_t M = 2;
+  while (M < 2 * N) M *= 2;
+  p->M = M;
+  p->log2M = ilog2_exact(M);
+
+  auto bail = [&](fst_status s) {
+    destroy_plan(p);
+    return s;
+  };
+
+  // twiddle tables (FP64, rounded copy for FP32)
+  {
+    std::vector<double2> hi, lo;
+    build_twiddles(hi, lo);
+    std::vector<float2> hi32(hi.size()), lo32(lo.size());
+    for (size_t i = 0; i < hi.size(); ++i) hi32[i] = make_float2((float)hi[i].x, (float)hi[i].y);
+    for (size_t i = 0; i < lo.size(); ++i) lo32[i] = make_float2((float)lo[i].x, (float)lo[i].y);
+    fst_status s;
+    if ((s = R->alloc((void **)&p->tw64h, hi.size() * sizeof(double2))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->tw64l, lo.size() * sizeof(double2))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->tw32h, hi.size() * sizeof(float2))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->tw32l, lo.size() * sizeof(float2))) != FST_OK) return bail(s);
+    if ((s = R->h2d(p->tw64h, hi.data(), hi.size() * sizeof(double2))) != FST_OK) return bail(s);
+    if ((s = R->h2d(p->tw64l, lo.data(), lo.size() * sizeof(double2))) != FST_OK) return bail(s);
+    if ((s = R->h2d(p->tw32h, hi32.data(), hi32.size() * sizeof(float2))) != FST_OK) return bail(s);
+    if ((s = R->h2d(p->tw32l, lo32.data(), lo32.size() * sizeof(float2))) != FST_OK) return bail(s);
+  }
+
+  Scoped sc(R);
+  const Layout L64 = make_layout(N, p->log2M, true, 0);
+  const Layout L32 = make_layout(N, p->log2M, false, 0);
+
+  // sinc spectrum: forward FFT (FP64) of the even embedding c of the first row of B
+  double *cvec, *spec_unit;
+  double2 *X;
+  {
+    fst_status s;
+    if ((s = sc.alloc(&cvec, (size_t)M)) != FST_OK) return bail(s);
+    if ((s = sc.alloc(&X, (size_t)M)) != FST_OK) return bail(s);
+    if ((s = sc.alloc(&spec_unit, (size_t)M)) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->spec64, (size_t)M * sizeof(double))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->spec32, (size_t)M * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->sinc_embed(cvec, N, M, W)) != FST_OK) return bail(s);
+    ConvArgs<double> a{};
+    a.y = cvec;
+    a.out = nullptr;
+    a.ld = M;
+    a.batch = 1;
+    a.cplx = 0;
+    a.N = M;
+    a.r = 0;
+    a.tw = plan_tw<double>(p);
+    a.mode = MODE_FORWARD;
+    Layout Lf = L64;
+    Lf.chunk = std::max<int64_t>(1, Lf.G);
+    if (!Lf.small) Lf.Pnz = 1 << Lf.log2P;
+    // forward output goes straight into X ([k1][k2] order for 3-pass, natural for small)
+    if (Lf.small) {
+      a.inter = X;
+      a.pair0 = 0;
+      a.npairs = 1;
+      a.log2M = Lf.log2M;
+      if ((s = R->small(a, Lf)) != FST_OK) return bail(s);
+    } else {
+      const size_t need = (size_t)Lf.chunk * M * sizeof(double2) + (size_t)Lf.chunk * Lf.ntiles * 2 * 8 +
+                          (size_t)Lf.chunk * 2 * 8 + 1024;
+      char *w;
+      if ((s = sc.alloc(&w, need)) != FST_OK) return bail(s);
+      if ((s = run_conv<double>(R, Lf, a, 1, w)) != FST_OK) return bail(s);
+      if ((s = R->d2d(X, w, (size_t)M * sizeof(double2))) != FST_OK) return bail(s);
+    }
+    // unit-scaled spectrum (for the eigenvalues) in the FP64 layout, then the
+    // operator's spectrum beta/M in both layouts
+    float *dummy32;
+    if ((s = sc.alloc(&dummy32, (size_t)M)) != FST_OK) return bail(s);
+    if ((s = R->spec_store(X, L64, L32, M, 1.0 / (double)M, spec_unit, dummy32)) != FST_OK) return bail(s);
+    if ((s = R->spec_store(X, L64, L32, M, p->beta / (double)M, p->spec64, p->spec32)) != FST_OK) return bail(s);
+  }
+
+  // eigen-window around the centre, widened until both edges are outside T
+  const int64_t centre = (op == FST_OP_TIKHONOV) ? Kdef : K;
+  int64_t Rw = (int64_t)std::min(ceil(cor1_bound(N, eps)), ceil(0.6 * asymptotic_transition(N, eps)) + 6.0);
+  Rw = std::max<int64_t>(Rw, 2);
+  std::vector<double> lamw;
+  double *S = nullptr;
+  int64_t lo = 0, hi = 0;
+  for (int attempt = 0;; ++attempt) {
+    lo = std::max<int64_t>(0, centre - Rw);
+    hi = std::min<int64_t>(N - 1, centre + Rw);
+    const int nwin = (int)(hi - lo + 1);
+    Scoped win(R);
+    double *Sw;
+    fst_status s;
+    if ((s = win.alloc(&Sw, (size_t)nwin * N)) != FST_OK) return bail(s);
+    lamw.assign(nwin, 0.0);
+    if ((s = window_vectors(p, win, lo, hi, Sw, lamw.data(), spec_unit)) != FST_OK) return bail(s);
+    const bool lo_ok = (lo == 0) || !in_T(lamw[0], lo, K, eps, op, p->alpha);
+    const bool hi_ok = (hi == N - 1) || !in_T(lamw[nwin - 1], hi, K, eps, op, p->alpha);
+    if (lo_ok && hi_ok) {
+      // keep the window's vectors: move ownership of Sw to sc
+      win.ptrs.erase(std::find(win.ptrs.begin(), win.ptrs.end(), (void *)Sw));
+      sc.ptrs.push_back(Sw);
+      S = Sw;
+      break;
+    }
+    if (attempt > 12) return bail(fail(FST_ENOCONVERGE, "eigen-window search did not terminate"));
+    Rw *= 2;
+  }
+  p->win_lo = lo;
+  p->win_hi = hi;
+  p->lam_window = lamw;
+
+  std::vector<int> sel;
+  for (int64_t l = lo; l <= hi; ++l) {
+    const double lam = lamw[l - lo];
+    if (in_T(lam, l, K, eps, op, p->alpha)) {
+      sel.push_back((int)(l - lo));
+      p->idx.push_back(l);
+      p->lam.push_back(lam);
+      p->D.push_back(D_of(lam, l, K, op, p->alpha));
+    }
+  }
+  p->r = (int64_t)sel.size();
+  p->rpad = std::max<int64_t>(4, (p->r + 3) / 4 * 4);
+  {
+    fst_status s;
+    const size_t nst = (size_t)N * p->rpad;
+    if ((s = R->alloc((void **)&p->ST64, nst * sizeof(double))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->ST32, nst * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->D64, (size_t)p->rpad * sizeof(double))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->D32, (size_t)p->rpad * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->zero(p->D64, (size_t)p->rpad * sizeof(double))) != FST_OK) return bail(s);
+    if (p->r > 0) {
+      int *dsel;
+      if ((s = sc.alloc(&dsel, sel.size())) != FST_OK) return bail(s);
+      if ((s = R->h2d(dsel, sel.data(), sel.size() * sizeof(int))) != FST_OK) return bail(s);
+      if ((s = R->gather_ST(S, N, dsel, (int)p->r, (int)p->rpad, p->ST64, p->ST32)) != FST_OK) return bail(s);
+      if ((s = R->h2d(p->D64, p->D.data(), p->D.size() * sizeof(double))) != FST_OK) return bail(s);
+    } else {
+      if ((s = R->zero(p->ST64, nst * sizeof(double))) != FST_OK) return bail(s);
+      if ((s = R->zero(p->ST32, nst * sizeof(float))) != FST_OK) return bail(s);
+    }
+    if ((s = R->to_f32(p->D64, p->D32, p->rpad)) != FST_OK) return bail(s);
+    if ((s = R->sync()) != FST_OK) return bail(s);
+  }
+  p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad);
+  p->lay64 = make_layout(N, p->log2M, true, (int)p->rpad);
+  if (p->lay32.small && p->lay32.smem_small > 227 * 1024)
+    return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
+  if (p->lay64.small && p->lay64.smem_small > 227 * 1024)
+    return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
+  *out = p;
+  return FST_OK;
+}
+
+void destroy_plan(fst_plan_t p) {
+  if (!p) return;
+  Runner *R = p->R;
+  if (R) {
+    R->sync();
+    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64,
+                    p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
+    for (void *b : bufs)
+      if (b) R->release(b);
+    delete R;
+  }
+  delete p;
+}
+
+}  // namespace fst
+
+using namespace fst;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *fst_last_error(void) { return g_err.c_str(); }
+const char *fst_version(void) { return "fst-gb300 0.1"; }
+
+fst_status fst_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op, double alpha,
+                       void *stream) {
+  Runner *R = make_dev_runner();
+  if (!R) return fail(FST_ECUDA, "no CUDA device");
+  R->set_stream(stream);
+  return build_plan(R, out, N, W, K, eps, op, alpha);
+}
+
+fst_status fst_plan(fst_plan_t *out, int64_t N, double W, int64_t K, double eps, void *stream) {
+  return fst_plan_op(out, N, W, K, eps, FST_OP_PROJECT, 0.0, stream);
+}
+
+fst_status fst_plan_info(fst_plan_t p, int64_t *K, int64_t *r, int64_t *M, int64_t *wlo, int64_t *whi) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (K) *K = p->K;
+  if (r) *r = p->r;
+  if (M) *M = p->M;
+  if (wlo) *wlo = p->win_lo;
+  if (whi) *whi = p->win_hi;
+  return FST_OK;
+}
+
+fst_status fst_plan_export(fst_plan_t p, int64_t *idx, double *lam, double *D, double *S_T) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  const int64_t r = p->r;
+  if (idx) memcpy(idx, p->idx.data(), r * sizeof(int64_t));
+  if (lam) memcpy(lam, p->lam.data(), r * sizeof(double));
+  if (D) memcpy(D, p->D.data(), r * sizeof(double));
+  if (S_T && r > 0) {
+    std::vector<double> rows((size_t)p->N * p->rpad);
+    fst_status s = p->R->d2h(rows.data(), p->ST64, rows.size() * sizeof(double));
+    if (s != FST_OK) return s;
+    for (int64_t j = 0; j < r; ++j)
+      for (int64_t n = 0; n < p->N; ++n) S_T[j * p->N + n] = rows[n * p->rpad + j];
+  }
+  return FST_OK;
+}
+
+fst_status fst_project(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype,
+                       void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  p->R->set_stream(stream);
+  return run_apply(p, y, out, batch, ld, dtype, true);
+}
+
+fst_status fst_apply_prolate(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype,
+                             void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  p->R->set_stream(stream);
+  return run_apply(p, y, out, batch, ld, dtype, false);
+}
+
+fst_status fst_destroy(fst_plan_t p) {
+  destroy_plan(p);
+  return FST_OK;
+}
+
+fst_status fst_reduced_tridiagonal(int64_t N, double W, int parity, int64_t *n, double *d, double *e) {
+  if (N < 1 || !(W > 0.0 && W < 0.5) || (parity != 0 && parity != 1) || !n)
+    return fail(FST_EINVAL, "bad arguments");
+  Reduced R = reduced_tridiagonal(N, W, parity);
+  *n = R.n;
+  if (d) memcpy(d, R.d.data(), R.n * sizeof(double));
+  if (e && R.n > 1) memcpy(e, R.e.data() + 1, (R.n - 1) * sizeof(double));
+  return FST_OK;
+}
+
+// ---- host emulation (tests) ----
+fst_status fst_emu_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op, double alpha) {
+  return build_plan(make_emu_runner(), out, N, W, K, eps, op, alpha);
+}
+
+int fst_plan_is_emulated(fst_plan_t p) { return (p && p->R && !p->R->device()) ? 1 : 0; }
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// fst_internal.h -- plan structure, launch layouts and the execution back-ends of
+// the fast Slepian projection library.
+//
+// All host logic (plan construction, launch sequencing) is written once against
+// the abstract Runner.  DevRunner (fst_device.cu) enqueues CUDA kernels on a
+// stream and owns device memory; EmuRunner (fst_emu.cu) executes the very same
+// kernel bodies on the host, one block at a time, for CPU tests.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fst.h"
+#include "fst_kernels.cuh"
+#include "fst_plan_kernels.cuh"
+
+namespace fst {
+
+// Launch layout of the length-M transform for one real type.
+struct Layout {
+  bool small = true;
+  int log2M = 0, log2P = 0, log2Q = 0;
+  int Pnz = 0, NB = 0, G = 1, ntiles = 0;
+  int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
+  size_t smem_small = 0, smem_A = 0, smem_B = 0, smem_C = 0;
+  int64_t chunk = 1;   // pairs per launch group
+};
+
+Layout make_layout(int64_t N, int log2M, bool dbl, int rpad);
+// position of natural frequency index k in the layout's spectrum array
+__host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
+  if (L.small) return k;
+  const int64_t P = 1LL << L.log2P;
+  return (k & (P - 1)) * (1LL << L.log2Q) + (k >> L.log2P);
+}
+
+struct Runner {
+  virtual ~Runner() {}
+  virtual bool device() const = 0;
+  virtual void set_stream(void *) {}
+  virtual void *stream() const { return nullptr; }
+  virtual fst_status alloc(void **p, size_t bytes) = 0;
+  virtual void release(void *p) = 0;
+  virtual fst_status h2d(void *dst, const void *src, size_t bytes) = 0;
+  virtual fst_status d2h(void *dst, const void *src, size_t bytes) = 0;  // synchronous
+  virtual fst_status d2d(void *dst, const void *src, size_t bytes) = 0;
+  virtual fst_status zero(void *p, size_t bytes) = 0;
+  virtual fst_status sync() = 0;
+
+  virtual fst_status small(const ConvArgs<float> &a, const Layout &L) = 0;
+  virtual fst_status small(const ConvArgs<double> &a, const Layout &L) = 0;
+  virtual fst_status passA(const ConvArgs<float> &a, const Layout &L) = 0;
+  virtual fst_status passA(const ConvArgs<double> &a, const Layout &L) = 0;
+  virtual fst_status reduce(const ConvArgs<float> &a, const Layout &L) = 0;
+  virtual fst_status reduce(const ConvArgs<double> &a, const Layout &L) = 0;
+  virtual fst_status passB(const ConvArgs<float> &a, const Layout &L) = 0;
+  virtual fst_status passB(const ConvArgs<double> &a, const Layout &L) = 0;
+  virtual fst_status passC(const ConvArgs<float> &a, const Layout &L) = 0;
+  virtual fst_status passC(const ConvArgs<double> &a, const Layout &L) = 0;
+
+  // plan kernels (all pointers in runner memory)
+  virtual fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo,
+                            double ghi, double pivmin, double *out, int *flag) = 0;
+  virtual fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol,
+                           int iters, double *x, double *fd, double *fdl, double *fdu, double *fdu2,
+                           uint8_t *piv) = 0;
+  virtual fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) = 0;
+  virtual fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) = 0;
+  virtual fst_status sinc_embed(double *c, int64_t N, int64_t M, double W) = 0;
+  virtual fst_status spec_store(const double2 *X, const Layout &L64, const Layout &L32, int64_t M, double scale,
+                                double *spec64, float *spec32) = 0;
+  virtual fst_status gather_ST(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64,
+                               float *ST32) = 0;
+  virtual fst_status to_f32(const double *src, float *dst, int64_t n) = 0;
+};
+
+Runner *make_dev_runner();
+Runner *make_emu_runner();
+
+}  // namespace fst
+
+struct fst_plan_s {
+  fst::Runner *R = nullptr;
+  int64_t N = 0, K = 0, M = 0, r = 0, rpad = 0, win_lo = 0, win_hi = 0;
+  int log2M = 0;
+  double W = 0, eps = 0, alpha = 0, beta = 1;
+  int op = 0;
+  fst::Layout lay32, lay64;
+  float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr;
+  double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
+  float2 *tw32h = nullptr, *tw32l = nullptr;
+  double2 *tw64h = nullptr, *tw64l = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<int64_t> idx;
+  std::vector<double> lam, D;
+  std::vector<double> lam_window;
+};
+
+namespace fst {
+void set_error(const std::string &msg);
+fst_status fail(fst_status st, const std::string &msg);
+// build a plan with the given runner (takes ownership of R)
+fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                      double alpha);
+// B y (+ correction when full) for `batch` signals in runner memory
+fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full);
+void destroy_plan(fst_plan_t p);
+}  // namespace fst

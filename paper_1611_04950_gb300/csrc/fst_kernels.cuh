@@ -1,0 +1,340 @@
+// fst_kernels.cuh -- bodies of the apply kernels of the fast Slepian projection
+//
+//     out = beta * B_{N,W} y + S_T (D o (S_T^T y))          (Section 1.3, Corollary 2)
+//
+// B_{N,W} y is the first N samples of a length-M circular convolution of the
+// zero-padded signal with the even sinc embedding c (c[k] = c[M-k] = b[k], k < N;
+// Section 4.1), done as FFT -> multiply by the real spectrum DFT_M(c)/M -> inverse FFT.
+// Real signals travel two at a time as the real and imaginary part of one complex
+// transform: the spectrum is real and even, so B acts on both parts separately and
+// the two results come back in the real and imaginary parts ("pairs").  A complex
+// signal is one pair.
+//
+// Two layouts of the length-M transform:
+//   small  (M <= one CTA's shared memory): one CTA per pair does everything.
+//   3-pass (M = P * Q):  n = n1 Q + n2, k = k1 + P k2 (four-step decomposition)
+//     pass A: per column n2, P-point DFT over n1, times W_M^{n2 k1}   -> inter[k1][n2]
+//             (+ the partial sums of S_T^T y over the tile, written per tile)
+//     reduce: c = sum of the partials in a fixed order, a = D o c
+//     pass B: per row k1, Q-point DFT over n2 (natural k2 order), times
+//             spec[k1 + P k2], inverse Q-point DFT, times W_M^{-n2 k1} -> inter[k1][n2]
+//     pass C: per column n2, inverse P-point DFT over k1 -> n1; the first N samples
+//             plus S_T a are written out.
+// No floating-point atomics anywhere: every sum has a fixed order, so results are
+// bit-for-bit repeatable.
+//
+// Each body is a sequence of phases separated by block barriers.  The device
+// executor (DevEx) runs one thread per phase call and __syncthreads() between
+// phases; the host executor (fst_emu.cu) loops the threads of a block, which lets
+// the CPU tests run these exact bodies.
+#pragma once
+#include "fst_fft.cuh"
+
+namespace fst {
+
+enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2 };
+
+template <typename T> struct ConvArgs {
+  // signals
+  const T *y;         // real: batch rows of N (stride ld); complex: batch rows of N pairs (stride ld pairs)
+  T *out;
+  int64_t ld;
+  int64_t batch;      // number of signals (real) or complex signals
+  int cplx;           // 0: real signals paired (2p, 2p+1); 1: complex signals
+  int64_t pair0;      // first global pair handled by this launch
+  int64_t npairs;     // pairs handled by this launch (local pair index < npairs)
+  int64_t N;
+  int log2M;
+  // 3-pass decomposition
+  int log2P, log2Q;
+  int Pnz;            // rows n1 with n1 * Q < N
+  int NB;             // columns per pair in a pass-A/C tile
+  int G;              // pairs per pass-A/C tile
+  // plan data
+  const T *spec;      // DFT_M(c) * beta / M, natural order (small) or [k1][k2] (3-pass)
+  const T *ST;        // [N][rpad], row n = (s_j[n])_j, zero padded
+  int r, rpad;
+  const T *D;         // [r]
+  Tw<T> tw;
+  // workspace (3-pass)
+  c2<T> *inter;       // [npairs][P][Q] (small, forward mode: [npairs][M])
+  T *part;            // [npairs][ntiles][2][rpad]
+  T *acoef;           // [npairs][2][rpad]: D o c for (re, im)
+  int mode;
+};
+
+template <typename T> struct KState {
+  c2<T> v[16];
+};
+
+// ---- signal access ---------------------------------------------------------
+template <typename T> FST_HD c2<T> load_pair(const ConvArgs<T> &a, int64_t pl, int64_t n) {
+  const int64_t p = a.pair0 + pl;
+  if (a.cplx) {
+    const c2<T> *y2 = reinterpret_cast<const c2<T> *>(a.y);
+    return y2[p * a.ld + n];
+  }
+  const int64_t s0 = 2 * p, s1 = 2 * p + 1;
+  const T re = a.y[s0 * a.ld + n];
+  const T im = (s1 < a.batch) ? a.y[s1 * a.ld + n] : (T)0;
+  return mk<T>(re, im);
+}
+template <typename T> FST_HD void store_pair(const ConvArgs<T> &a, int64_t pl, int64_t n, c2<T> v) {
+  const int64_t p = a.pair0 + pl;
+  if (a.cplx) {
+    reinterpret_cast<c2<T> *>(a.out)[p * a.ld + n] = v;
+    return;
+  }
+  const int64_t s0 = 2 * p, s1 = 2 * p + 1;
+  a.out[s0 * a.ld + n] = v.x;
+  if (s1 < a.batch) a.out[s1 * a.ld + n] = v.y;
+}
+
+// correction epilogue value: S_T[n,:] . (a_re, a_im)
+template <typename T> FST_HD c2<T> corr_value(const ConvArgs<T> &a, int64_t n, const T *are, const T *aim) {
+  const T *row = a.ST + n * a.rpad;
+  T zr = 0, zi = 0;
+  for (int j = 0; j < a.r; ++j) {
+    const T s = ldg(row + j);
+    zr += s * are[j];
+    zi += s * aim[j];
+  }
+  return mk<T>(zr, zi);
+}
+
+// ---- small: one CTA per pair, M <= shared-memory capacity ----------------------
+// smem: buf[padded_size(M)] complex, red[nwarps][2][64] reals, coef[2][rpad] reals
+template <typename T, typename Ex>
+FST_HD void small_body(Ex &ex, const ConvArgs<T> &a, int64_t pl, c2<T> *buf, T *red, T *coef) {
+  using St = typename Ex::State;
+  const int log2L = a.log2M;
+  const int L = 1 << log2L;
+  const int N = (int)a.N;
+  const int nthr = ex.nthr;
+  const int nwarps = (nthr + 31) / 32;
+
+  ex.phase([&](int tid, St &) {
+    for (int i = tid; i < L; i += nthr) buf[pad(i)] = (i < N) ? load_pair(a, pl, i) : mk<T>(0, 0);
+  });
+
+  const bool corr = (a.mode == MODE_FULL) && a.r > 0;
+  for (int j0 = 0; corr && j0 < a.r; j0 += 64) {
+    // warps split the samples, lanes split j: red[w][c][jj] = sum over the warp's samples
+    ex.phase([&](int tid, St &) {
+      const int w = tid >> 5, lane = tid & 31;
+      T acc[4] = {0, 0, 0, 0};
+      const int ja = j0 + lane, jb = j0 + lane + 32;
+      for (int i = w; i < N; i += nwarps) {
+        const c2<T> v = buf[pad(i)];
+        const T *row = a.ST + (int64_t)i * a.rpad;
+        const T sa = (ja < a.r) ? ldg(row + ja) : (T)0;
+        const T sb = (jb < a.r) ? ldg(row + jb) : (T)0;
+        acc[0] += sa * v.x; acc[1] += sa * v.y;
+        acc[2] += sb * v.x; acc[3] += sb * v.y;
+      }
+      T *rw = red + w * 128;
+      rw[lane] = acc[0]; rw[64 + lane] = acc[1];
+      rw[32 + lane] = acc[2]; rw[96 + lane] = acc[3];
+    });
+    ex.phase([&](int tid, St &) {
+      for (int t = tid; t < 128; t += nthr) {
+        const int c = t >> 6, jj = t & 63;
+        T s = 0;
+        for (int w = 0; w < nwarps; ++w) s += red[w * 128 + c * 64 + jj];
+        const int j = j0 + jj;
+        if (j < a.r) coef[c * a.rpad + j] = ldg(a.D + j) * s;
+      }
+    });
+  }
+
+  tile_fft<T, false>(ex, buf, log2L, 1, a.tw);
+
+  if (a.mode == MODE_FORWARD) {
+    ex.phase([&](int tid, St &) {
+      for (int i = tid; i < L; i += nthr) a.inter[pl * L + i] = buf[pad(i)];
+    });
+    return;
+  }
+
+  ex.phase([&](int tid, St &) {
+    for (int i = tid; i < L; i += nthr) buf[pad(i)] = cscale(buf[pad(i)], ldg(a.spec + i));
+  });
+
+  tile_fft<T, true>(ex, buf, log2L, 1, a.tw);
+
+  ex.phase([&](int tid, St &) {
+    for (int i = tid; i < N; i += nthr) {
+      c2<T> v = buf[pad(i)];
+      if (corr) v = cadd(v, corr_value(a, i, coef, coef + a.rpad));
+      store_pair(a, pl, i, v);
+    }
+  });
+}
+
+// ---- pass A: forward column DFTs over n1 for a tile of G pairs x NB columns ----
+// tile element (n1, col), col = g * NB + c, lives at buf[pad(n1 * ncols + col)]
+// smem: buf[padded_size(P * ncols)] complex, red[nwarps][2][64] reals
+template <typename T, typename Ex>
+FST_HD void passA_body(Ex &ex, const ConvArgs<T> &a, int64_t tile, int64_t group, c2<T> *buf, T *red) {
+  using St = typename Ex::State;
+  const int P = 1 << a.log2P;
+  const int Q = 1 << a.log2Q;
+  const int ncols = a.G * a.NB;
+  const int nthr = ex.nthr;
+  const int nwarps = (nthr + 31) / 32;
+  const int64_t n2_0 = tile * a.NB;
+  const int64_t g0 = group * a.G;
+  const int ntiles = Q / a.NB;
+
+  ex.phase([&](int tid, St &) {
+    for (int e = tid; e < P * ncols; e += nthr) {
+      const int n1 = e / ncols, col = e % ncols;
+      const int g = col / a.NB, c = col % a.NB;
+      const int64_t n = (int64_t)n1 * Q + n2_0 + c;
+      c2<T> v = mk<T>(0, 0);
+      if (n1 < a.Pnz && n < a.N && g0 + g < a.npairs) v = load_pair(a, g0 + g, n);
+      buf[pad(e)] = v;
+    }
+  });
+
+  if (a.mode == MODE_FULL && a.r > 0) {
+    // warps of pair g: w = g * wpp + u, u < wpp; lanes split j (j = lane, lane + 32)
+    const int wpp = nwarps / a.G;  // host guarantees nwarps % G == 0
+    const int nel = a.Pnz * a.NB;
+    for (int j0 = 0; j0 < a.r; j0 += 64) {
+      ex.phase([&](int tid, St &) {
+        const int w = tid >> 5, lane = tid & 31;
+        const int g = w / wpp, u = w % wpp;
+        T acc[4] = {0, 0, 0, 0};
+        const int ja = j0 + lane, jb = j0 + lane + 32;
+        for (int e = u; e < nel; e += wpp) {
+          const int n1 = e / a.NB, c = e % a.NB;
+          const int64_t n = (int64_t)n1 * Q + n2_0 + c;
+          if (n >= a.N) continue;
+          const c2<T> v = buf[pad(n1 * ncols + g * a.NB + c)];
+          const T *row = a.ST + n * a.rpad;
+          const T sa = (ja < a.r) ? ldg(row + ja) : (T)0;
+          const T sb = (jb < a.r) ? ldg(row + jb) : (T)0;
+          acc[0] += sa * v.x; acc[1] += sa * v.y;
+          acc[2] += sb * v.x; acc[3] += sb * v.y;
+        }
+        T *rw = red + w * 128;
+        rw[lane] = acc[0]; rw[64 + lane] = acc[1];
+        rw[32 + lane] = acc[2]; rw[96 + lane] = acc[3];
+      });
+      ex.phase([&](int tid, St &) {
+        for (int t = tid; t < a.G * 128; t += nthr) {
+          const int g = t / 128, c = (t % 128) / 64, jj = t % 64;
+          const int j = j0 + jj;
+          if (j >= a.r || g0 + g >= a.npairs) continue;
+          T s = 0;
+          for (int u = 0; u < wpp; ++u) s += red[(g * wpp + u) * 128 + c * 64 + jj];
+          a.part[(((g0 + g) * ntiles + tile) * 2 + c) * a.rpad + j] = s;
+        }
+      });
+    }
+  }
+
+  tile_fft<T, false>(ex, buf, a.log2P, ncols, a.tw);
+
+  ex.phase([&](int tid, St &) {
+    for (int e = tid; e < P * ncols; e += nthr) {
+      const int k1 = e / ncols, col = e % ncols;
+      const int g = col / a.NB, c = col % a.NB;
+      if (g0 + g >= a.npairs) continue;
+      const int64_t n2 = n2_0 + c;
+      const c2<T> w = a.tw.template root<false>((uint64_t)n2 * (uint64_t)k1, a.log2M);
+      a.inter[((g0 + g) * P + k1) * (int64_t)Q + n2] = cmul(buf[pad(e)], w);
+    }
+  });
+}
+
+// ---- reduce: a[pair][c][j] = D_j * sum over tiles of part[pair][tile][c][j] ---------
+template <typename T>
+FST_HD void reduce_body(const ConvArgs<T> &a, int64_t pl, int tid, int nthr) {
+  const int Q = 1 << a.log2Q;
+  const int ntiles = Q / a.NB;
+  for (int t = tid; t < 2 * a.r; t += nthr) {
+    const int c = t / a.r, j = t % a.r;
+    T s = 0;
+    for (int tile = 0; tile < ntiles; ++tile) s += a.part[((pl * ntiles + tile) * 2 + c) * a.rpad + j];
+    a.acoef[(pl * 2 + c) * a.rpad + j] = ldg(a.D + j) * s;
+  }
+}
+
+// ---- pass B: row k1 of pair pl: forward Q-point DFT, spectrum, inverse, twiddle -----
+// smem: buf[padded_size(Q)] complex
+template <typename T, typename Ex>
+FST_HD void passB_body(Ex &ex, const ConvArgs<T> &a, int64_t pl, int k1, c2<T> *buf) {
+  using St = typename Ex::State;
+  const int P = 1 << a.log2P;
+  const int Q = 1 << a.log2Q;
+  const int nthr = ex.nthr;
+  c2<T> *row = a.inter + ((pl * P) + k1) * (int64_t)Q;
+
+  ex.phase([&](int tid, St &) {
+    for (int i = tid; i < Q; i += nthr) buf[pad(i)] = row[i];
+  });
+  tile_fft<T, false>(ex, buf, a.log2Q, 1, a.tw);
+  if (a.mode == MODE_FORWARD) {
+    ex.phase([&](int tid, St &) {
+      for (int i = tid; i < Q; i += nthr) row[i] = buf[pad(i)];
+    });
+    return;
+  }
+  ex.phase([&](int tid, St &) {
+    const T *sp = a.spec + (int64_t)k1 * Q;
+    for (int i = tid; i < Q; i += nthr) buf[pad(i)] = cscale(buf[pad(i)], ldg(sp + i));
+  });
+  tile_fft<T, true>(ex, buf, a.log2Q, 1, a.tw);
+  ex.phase([&](int tid, St &) {
+    for (int i = tid; i < Q; i += nthr) {
+      const c2<T> w = a.tw.template root<true>((uint64_t)i * (uint64_t)k1, a.log2M);
+      row[i] = cmul(buf[pad(i)], w);
+    }
+  });
+}
+
+// ---- pass C: inverse column DFTs over k1, first N samples + correction ----------------
+// smem: buf[padded_size(P * ncols)] complex; the coefficients a = D o c are read
+// from global memory (L1-resident broadcast)
+template <typename T, typename Ex>
+FST_HD void passC_body(Ex &ex, const ConvArgs<T> &a, int64_t tile, int64_t group, c2<T> *buf) {
+  using St = typename Ex::State;
+  const int P = 1 << a.log2P;
+  const int Q = 1 << a.log2Q;
+  const int ncols = a.G * a.NB;
+  const int nthr = ex.nthr;
+  const int64_t n2_0 = tile * a.NB;
+  const int64_t g0 = group * a.G;
+  const bool corr = (a.mode == MODE_FULL) && a.r > 0;
+
+  ex.phase([&](int tid, St &) {
+    for (int e = tid; e < P * ncols; e += nthr) {
+      const int k1 = e / ncols, col = e % ncols;
+      const int g = col / a.NB, c = col % a.NB;
+      c2<T> v = mk<T>(0, 0);
+      if (g0 + g < a.npairs) v = a.inter[((g0 + g) * P + k1) * (int64_t)Q + n2_0 + c];
+      buf[pad(e)] = v;
+    }
+  });
+
+  tile_fft<T, true>(ex, buf, a.log2P, ncols, a.tw);
+
+  ex.phase([&](int tid, St &) {
+    for (int e = tid; e < a.Pnz * ncols; e += nthr) {
+      const int n1 = e / ncols, col = e % ncols;
+      const int g = col / a.NB, c = col % a.NB;
+      const int64_t n = (int64_t)n1 * Q + n2_0 + c;
+      if (n >= a.N || g0 + g >= a.npairs) continue;
+      c2<T> v = buf[pad(e)];
+      if (corr) {
+        const T *cg = a.acoef + (g0 + g) * 2 * a.rpad;
+        v = cadd(v, corr_value(a, n, cg, cg + a.rpad));
+      }
+      store_pair(a, g0 + g, n, v);
+    }
+  });
+}
+
+}  // namespace fst

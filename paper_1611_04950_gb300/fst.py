@@ -1,0 +1,282 @@
+"""GB300-native fast Slepian projection (Karnik, Zhu, Wakin, Romberg, Davenport,
+"The Fast Slepian Transform", arXiv:1611.04950).
+
+Thin Python binding of the C ABI in include/fst.h (libfst_gb300.so): argument
+marshalling only.  Every step of the computation runs in the library's CUDA
+kernels; there is no Python or CPU fallback.  If the shared library has not been
+built, importing the binding raises -- build it with
+``python -m paper_1611_04950_gb300.build``.
+
+The functions carry the C names (fst_plan, fst_plan_op, fst_plan_info,
+fst_plan_export, fst_project, fst_project_host, fst_apply_prolate, fst_destroy,
+fst_last_error); ``Plan`` wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libfst_gb300.so")
+
+FST_OK, FST_EINVAL, FST_ENOMEM, FST_ECUDA, FST_ENOCONVERGE, FST_ETIMEOUT, FST_EUNSUPPORTED = range(7)
+FST_F32, FST_F64, FST_C64, FST_C128 = range(4)
+FST_OP_PROJECT, FST_OP_PINV, FST_OP_TIKHONOV = range(3)
+_OPS = {"project": FST_OP_PROJECT, "pinv": FST_OP_PINV, "tikhonov": FST_OP_TIKHONOV}
+_STATUS = {0: "FST_OK", 1: "FST_EINVAL", 2: "FST_ENOMEM", 3: "FST_ECUDA", 4: "FST_ENOCONVERGE",
+           5: "FST_ETIMEOUT", 6: "FST_EUNSUPPORTED"}
+
+# every symbol include/fst.h and include/fst_testing.h declare
+EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_project",
+            "fst_project_host", "fst_apply_prolate", "fst_destroy", "fst_last_error", "fst_version",
+            "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
+            "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read"]
+
+
+class FSTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1611_04950_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P, i64, d, vp, I = C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int
+    sig = {
+        "fst_plan": ([C.POINTER(P), i64, d, i64, d, vp], I),
+        "fst_plan_op": ([C.POINTER(P), i64, d, i64, d, I, d, vp], I),
+        "fst_plan_info": ([P] + [C.POINTER(i64)] * 5, I),
+        "fst_plan_export": ([P, C.POINTER(i64), C.POINTER(d), C.POINTER(d), C.POINTER(d)], I),
+        "fst_project": ([P, vp, vp, i64, i64, I, vp], I),
+        "fst_project_host": ([P, vp, vp, i64, I, vp], I),
+        "fst_apply_prolate": ([P, vp, vp, i64, i64, I, vp], I),
+        "fst_destroy": ([P], I),
+        "fst_last_error": ([], C.c_char_p),
+        "fst_version": ([], C.c_char_p),
+        "fst_reduced_tridiagonal": ([i64, d, I, C.POINTER(i64), C.POINTER(d), C.POINTER(d)], I),
+        "fst_emu_plan_op": ([C.POINTER(P), i64, d, i64, d, I, d], I),
+        "fst_plan_is_emulated": ([P], I),
+        "fst_launch_count": ([], C.c_longlong),
+        "fst_profile_enable": ([I], I),
+        "fst_profile_count": ([], I),
+        "fst_profile_read": ([I, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(st: int):
+    if st != FST_OK:
+        raise FSTError(st, _lib.fst_last_error().decode())
+
+
+# ---- C-named functions -------------------------------------------------------
+
+def fst_last_error() -> str:
+    return _lib.fst_last_error().decode()
+
+
+def fst_version() -> str:
+    return _lib.fst_version().decode()
+
+
+def fst_plan(N: int, W: float, K: int = -1, eps: float = 1e-6, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_lib.fst_plan(C.byref(h), N, W, K, eps, C.c_void_p(stream)))
+    return h.value
+
+
+def fst_plan_op(N: int, W: float, K: int, eps: float, op: int, alpha: float = 0.0, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_lib.fst_plan_op(C.byref(h), N, W, K, eps, op, alpha, C.c_void_p(stream)))
+    return h.value
+
+
+def fst_emu_plan_op(N: int, W: float, K: int, eps: float, op: int = FST_OP_PROJECT, alpha: float = 0.0) -> int:
+    h = C.c_void_p()
+    _check(_lib.fst_emu_plan_op(C.byref(h), N, W, K, eps, op, alpha))
+    return h.value
+
+
+def fst_plan_info(h: int) -> dict:
+    v = [C.c_int64() for _ in range(5)]
+    _check(_lib.fst_plan_info(C.c_void_p(h), *[C.byref(x) for x in v]))
+    return {"K": v[0].value, "r": v[1].value, "M": v[2].value, "window": (v[3].value, v[4].value)}
+
+
+def fst_plan_export(h: int, N: int, with_vectors: bool = True) -> dict:
+    r = fst_plan_info(h)["r"]
+    idx = np.zeros(max(r, 1), np.int64)
+    lam = np.zeros(max(r, 1))
+    D = np.zeros(max(r, 1))
+    S = np.zeros((max(r, 1), N)) if with_vectors else None
+    ptr = lambda a, t: a.ctypes.data_as(C.POINTER(t)) if a is not None else None
+    _check(_lib.fst_plan_export(C.c_void_p(h), ptr(idx, C.c_int64), ptr(lam, C.c_double), ptr(D, C.c_double),
+                                ptr(S, C.c_double)))
+    out = {"idx": idx[:r], "lam": lam[:r], "D": D[:r]}
+    if with_vectors:
+        out["S_T"] = S[:r].T.copy()
+    return out
+
+
+def fst_project(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dtype: int, stream: int = 0):
+    _check(_lib.fst_project(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, ld, dtype,
+                            C.c_void_p(stream)))
+
+
+def fst_apply_prolate(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dtype: int, stream: int = 0):
+    _check(_lib.fst_apply_prolate(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, ld, dtype,
+                                  C.c_void_p(stream)))
+
+
+def fst_project_host(h: int, y_ptr: int, out_ptr: int, batch: int, dtype: int, stream: int = 0):
+    _check(_lib.fst_project_host(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, dtype,
+                                 C.c_void_p(stream)))
+
+
+def fst_destroy(h: int):
+    _check(_lib.fst_destroy(C.c_void_p(h)))
+
+
+def fst_launch_count() -> int:
+    return int(_lib.fst_launch_count())
+
+
+def fst_profile_enable(on: bool = True):
+    _check(_lib.fst_profile_enable(1 if on else 0))
+
+
+def fst_profile_records() -> list:
+    """[(kernel name, ms, pairs)] of the launches recorded since fst_profile_enable."""
+    out = []
+    for i in range(_lib.fst_profile_count()):
+        nm, ms, un = C.c_char_p(), C.c_double(), C.c_longlong()
+        _check(_lib.fst_profile_read(i, C.byref(nm), C.byref(ms), C.byref(un)))
+        out.append((nm.value.decode(), ms.value, un.value))
+    return out
+
+
+def fst_plan_is_emulated(h: int) -> bool:
+    return bool(_lib.fst_plan_is_emulated(C.c_void_p(h)))
+
+
+def fst_reduced_tridiagonal(N: int, W: float, parity: int):
+    n = C.c_int64()
+    _check(_lib.fst_reduced_tridiagonal(N, W, parity, C.byref(n), None, None))
+    d = np.zeros(max(n.value, 1))
+    e = np.zeros(max(n.value - 1, 1))
+    _check(_lib.fst_reduced_tridiagonal(N, W, parity, C.byref(n),
+                                        d.ctypes.data_as(C.POINTER(C.c_double)),
+                                        e.ctypes.data_as(C.POINTER(C.c_double))))
+    return d[: n.value], e[: max(n.value - 1, 0)]
+
+
+# ---- torch / numpy convenience -------------------------------------------------
+
+def _dtype_code(dt) -> int:
+    import torch
+    m = {torch.float32: FST_F32, torch.float64: FST_F64, torch.complex64: FST_C64,
+         torch.complex128: FST_C128,
+         np.dtype(np.float32): FST_F32, np.dtype(np.float64): FST_F64,
+         np.dtype(np.complex64): FST_C64, np.dtype(np.complex128): FST_C128}
+    if dt not in m:
+        raise TypeError(f"unsupported dtype {dt}")
+    return m[dt]
+
+
+class Plan:
+    """Owns an fst plan.  ``emulate=True`` builds it on the host emulator (CPU tests:
+    signals are then numpy arrays or CPU tensors)."""
+
+    def __init__(self, N: int, W: float, K: int | None = None, eps: float = 1e-6, op: str = "project",
+                 alpha: float = 0.0, stream=None, emulate: bool = False):
+        self.N, self.W, self.eps, self.op, self.alpha = int(N), float(W), float(eps), op, float(alpha)
+        k = -1 if K is None else int(K)
+        self.emulated = emulate
+        if emulate:
+            self.h = fst_emu_plan_op(self.N, self.W, k, self.eps, _OPS[op], self.alpha)
+        else:
+            self.h = fst_plan_op(self.N, self.W, k, self.eps, _OPS[op], self.alpha, _stream_handle(stream))
+        info = fst_plan_info(self.h)
+        self.K, self.r, self.M, self.window = info["K"], info["r"], info["M"], info["window"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            fst_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, with_vectors: bool = True) -> dict:
+        return fst_plan_export(self.h, self.N, with_vectors)
+
+    def _run(self, fn, y, out, stream):
+        if self.emulated:
+            y = np.ascontiguousarray(np.asarray(y))
+            if y.ndim == 1:
+                y = y[None]
+            out = np.empty_like(y) if out is None else out
+            fn(self.h, y.ctypes.data, out.ctypes.data, y.shape[0], y.shape[1], _dtype_code(y.dtype), 0)
+            return out
+        import torch
+        if y.dim() == 1:
+            y = y.unsqueeze(0)
+        if y.shape[-1] != self.N or y.stride(-1) != 1:
+            raise ValueError("signals must be (batch, N) with unit stride along N")
+        if out is None:
+            out = torch.empty_like(y)
+        ld = y.stride(0) if y.shape[0] > 1 else self.N
+        if out.stride(0) != ld and out.shape[0] > 1:
+            raise ValueError("out must have the same row stride as y")
+        fn(self.h, y.data_ptr(), out.data_ptr(), y.shape[0], ld, _dtype_code(y.dtype), _stream_handle(stream))
+        return out
+
+    def project(self, y, out=None, stream=None):
+        """P_fast y (B y + S_T (D o S_T^T y)) for a (batch, N) device tensor."""
+        return self._run(fst_project, y, out, stream)
+
+    def apply_prolate(self, y, out=None, stream=None):
+        """B_{N,W} y alone."""
+        return self._run(fst_apply_prolate, y, out, stream)
+
+    def project_host(self, y, out=None, stream=None):
+        """P_fast y for a (batch, N) HOST array / tensor (copies inside the call)."""
+        import torch
+        if isinstance(y, np.ndarray):
+            y = torch.from_numpy(y)
+        if y.dim() == 1:
+            y = y.unsqueeze(0)
+        y = y.contiguous()
+        if out is None:
+            out = torch.empty_like(y)
+        fst_project_host(self.h, y.data_ptr(), out.data_ptr(), y.shape[0], _dtype_code(y.dtype),
+                         _stream_handle(stream))
+        return out
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream

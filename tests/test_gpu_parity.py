@@ -1,0 +1,210 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (per signal, 2-norm, relative to ||y||):
+  * against the oracle's fast projection at the same eps (same method, FP64):
+    FP64 path 1e-12, FP32 path 1e-5 (FP32 FFT of length M ~ 2^17..2^23 rounds at
+    ~1e-7 per element; 1e-5 is the stated FP32 budget);
+  * against the plain definition S_K S_K^T y: eps + 1e-12 (FP64) and eps + 1e-5
+    (FP32), the Corollary 2 bound plus the rounding budget.
+The transition set T is an integer decision taken from FP64 eigenvalues on both
+sides; it must agree exactly.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1611_04950_gb300 import fst as F  # noqa: E402
+from paper_1611_04950_gb300 import workloads  # noqa: E402
+from oracle import fst_oracle as O  # noqa: E402
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@functools.lru_cache(maxsize=None)
+def oplan(N, W, K, eps, op="project", alpha=0.0):
+    return O.make_plan(N, W, K, eps, op=op, alpha=alpha)
+
+
+def rel_err(out, ref, y):
+    out = np.asarray(out, dtype=np.complex128 if np.iscomplexobj(out) else np.float64)
+    return np.linalg.norm(out - ref, axis=1) / np.linalg.norm(y, axis=1)
+
+
+# ---------------------------------------------------------------- plan ------------
+
+@pytest.mark.parametrize("N,W,eps", [(4096, 1 / 16, 1e-6), (65536, 1 / 8, 1e-4), (1000, 1 / 64, 1e-8),
+                                     (12345, 0.3, 1e-3), (777, 0.45, 1e-12), (1, 0.3, 1e-6), (2, 0.1, 1e-6)])
+def test_plan_matches_oracle(N, W, eps):
+    _cuda()
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    ex = p.export()
+    assert p.K == O.default_K(N, W)
+    assert p.r == o.r
+    assert np.array_equal(ex["idx"], o.idx)
+    assert np.max(np.abs(ex["lam"] - o.lam), initial=0) < 1e-12
+    if p.r:
+        assert np.max(np.abs(ex["S_T"] - o.S_T)) < 1e-9
+
+
+# ---------------------------------------------------------------- tiny (FP64 + FP32) ----
+
+@functools.lru_cache(maxsize=None)
+def tiny_exact():
+    wl = workloads.tiny()
+    y = wl.y.numpy()
+    return wl, y, O.exact_project(wl.N, wl.W, O.default_K(wl.N, wl.W), y.T).T
+
+
+def test_tiny_fp64_and_fp32_against_exact_and_fast():
+    dev = _cuda()
+    wl, y, exact = tiny_exact()
+    p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    o = oplan(wl.N, wl.W, p.K, wl.eps)
+    fast = O.fast_project(o, y.T).T
+    yd = torch.as_tensor(y, device=dev)
+    out64 = p.project(yd).cpu().numpy()
+    out32 = p.project(yd.float()).cpu().numpy()
+    assert np.all(rel_err(out64, fast, y) < 1e-12)
+    assert np.all(rel_err(out32, fast, y) < 1e-5)
+    assert np.all(rel_err(out64, exact, y) <= wl.eps + 1e-12)
+    assert np.all(rel_err(out32, exact, y) <= wl.eps + 1e-5)
+
+
+# ---------------------------------------------------------------- N = 65536 -------------
+
+def test_c65k_small_batch():
+    dev = _cuda()
+    wl = workloads.c65k(batch=6)
+    p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    o = oplan(wl.N, wl.W, p.K, wl.eps)
+    y = wl.y.numpy().astype(np.float64)
+    fast = O.fast_project(o, y.T).T
+    out = p.project(wl.y.to(dev)).cpu().numpy()
+    assert np.all(rel_err(out, fast, y) < 1e-5)
+    ref = O.fast_project(oplan(wl.N, wl.W, p.K, O.EPS_REF), y.T).T   # within 1e-13 of S_K S_K^T y
+    assert np.all(rel_err(out, ref, y) <= wl.eps + 1e-5)
+
+
+def test_c65k_full_batch_sampled():
+    # the benchmark's launch configuration: 1024 signals in one call, samples checked
+    dev = _cuda()
+    wl = workloads.c65k(batch=1024, device="cuda")
+    p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    out = p.project(wl.y)
+    torch.cuda.synchronize()
+    o = oplan(wl.N, wl.W, p.K, wl.eps)
+    idx = [0, 1, 511, 512, 513, 1023]
+    y = wl.y[idx].double().cpu().numpy()
+    fast = O.fast_project(o, y.T).T
+    e = rel_err(out[idx].cpu().numpy(), fast, y)
+    assert np.all(e < 1e-5), e
+    assert torch.isfinite(out).all()
+
+
+# ---------------------------------------------------------------- edge cases ------------
+
+@pytest.mark.parametrize("N,W,eps", [(1, 0.3, 1e-6), (3, 0.2, 1e-6), (17, 0.05, 1e-3), (1000, 1 / 64, 1e-8),
+                                     (4097, 0.2, 1e-6), (8192, 0.25, 1e-8), (8193, 0.1, 1e-6),
+                                     (30001, 0.17, 1e-6), (131072, 1 / 64, 1e-3)])
+def test_ragged_lengths_fp32_fp64(N, W, eps):
+    dev = _cuda()
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    y = workloads.gaussian(3, N, seed=N)          # odd batch
+    fast = O.fast_project(o, y.numpy().T).T
+    out64 = p.project(y.to(dev)).cpu().numpy()
+    out32 = p.project(y.float().to(dev)).cpu().numpy()
+    assert np.all(rel_err(out64, fast, y.numpy()) < 1e-12)
+    assert np.all(rel_err(out32, fast, y.numpy()) < 1e-5)
+
+
+def test_complex_signals():
+    dev = _cuda()
+    N, W, eps = 20000, 0.05, 1e-6
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    y = workloads.gaussian(4, N, seed=3, complex_=True)
+    fast = O.fast_project(o, y.numpy().T).T
+    out128 = p.project(y.to(dev)).cpu().numpy()
+    out64 = p.project(y.to(torch.complex64).to(dev)).cpu().numpy()
+    assert np.all(rel_err(out128, fast, y.numpy()) < 1e-12)
+    assert np.all(rel_err(out64, fast, y.numpy()) < 1e-5)
+
+
+def test_apply_prolate_direct_sum():
+    dev = _cuda()
+    N, W = 2049, 0.21
+    p = F.Plan(N, W, eps=1e-6)
+    y = workloads.gaussian(2, N, seed=1)
+    out = p.apply_prolate(y.to(dev)).cpu().numpy()
+    ref = O.apply_prolate_direct(y.numpy().T, W).T
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.sqrt(N)
+
+
+@pytest.mark.parametrize("op,alpha,mul", [("pinv", 0.0, 3.0), ("tikhonov", 1e-3, 1.0)])
+def test_other_operators(op, alpha, mul):
+    dev = _cuda()
+    N, W, eps = 600, 0.2, 1e-5
+    p = F.Plan(N, W, eps=eps, op=op, alpha=alpha)
+    o = oplan(N, W, p.K, eps, op, alpha)
+    assert p.r == o.r
+    y = workloads.gaussian(2, N, seed=8)
+    out = p.project(y.to(dev)).cpu().numpy()
+    assert np.max(np.abs(out - O.fast_apply(o, y.numpy().T).T)) < 1e-10
+    exact = O.exact_operator_dense(N, W, p.K, op, alpha)
+    assert np.all(rel_err(out, (exact @ y.numpy().T).T, y.numpy()) <= mul * eps + 1e-10)
+
+
+def test_degenerate_K_and_batch_zero():
+    dev = _cuda()
+    N, W = 200, 0.1
+    y = workloads.gaussian(2, N, seed=2).to(dev)
+    for K, want in ((0, torch.zeros_like(y)), (N, y)):
+        p = F.Plan(N, W, K=K, eps=1e-6)
+        out = p.project(y)
+        assert torch.all(torch.linalg.vector_norm(out - want, dim=1) <= 1e-6 * torch.linalg.vector_norm(y, dim=1) + 1e-12)
+    p = F.Plan(N, W, eps=1e-6)
+    F.fst_project(p.h, y.data_ptr(), y.data_ptr(), 0, N, F.FST_F64, 0)
+
+
+def test_strided_inplace_and_host_entry_point():
+    dev = _cuda()
+    N, W = 40000, 0.125
+    p = F.Plan(N, W, eps=1e-4)
+    y = workloads.gaussian(5, N + 7, seed=4).float().to(dev)
+    view = y[:, :N]
+    out = torch.zeros_like(y)
+    F.fst_project(p.h, view.data_ptr(), out.data_ptr(), 5, N + 7, F.FST_F32,
+                  torch.cuda.current_stream().cuda_stream)
+    dense = p.project(view.contiguous())
+    torch.cuda.synchronize()
+    assert torch.equal(out[:, :N], dense)
+    assert torch.all(out[:, N:] == 0)
+    host = view.contiguous().cpu().pin_memory()
+    hout = p.project_host(host)
+    assert torch.equal(hout, dense.cpu())
+    z = view.contiguous().clone()
+    F.fst_project(p.h, z.data_ptr(), z.data_ptr(), 5, N, F.FST_F32, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.equal(z, dense)
+
+
+def test_repeatable_bit_for_bit():
+    dev = _cuda()
+    N, W = 65536, 0.25
+    p = F.Plan(N, W, eps=1e-8)
+    y = workloads.gaussian(8, N, seed=12).float().to(dev)
+    a = p.project(y)
+    b = p.project(y)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
