@@ -163,6 +163,30 @@ fst_status fst_reduced_tridiagonal(int64_t N, double W, int parity, int64_t *n,
                                    double *d, double *e);
 
 /*
+ * fst_project_noalloc -- fst_project that allocates nothing.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc or cudaFree
+ * when they project (code recorded into a CUDA graph, or a process whose memory
+ * manager owns all device memory after start-up).  fst_project allocates its
+ * scratch on demand on the plan's first call; this variant instead uses one
+ * fixed array of fst_noalloc_scratch_bytes() = 128 MiB compiled into the
+ * library (every GPU that loads the library holds it until the process exits).
+ *   Arguments, layout and results: as fst_project (device pointers).  The plan
+ *   itself must already exist (fst_plan allocates).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture.
+ *   Sharing: all calls share the one array and it keeps the last call's contents.
+ *   Calls whose work overlaps on the GPU (different streams, or several host
+ *   threads) race on it: serialise them.  Nothing in it needs clearing.
+ *   Errors: as fst_project; FST_EINVAL (message "signal too long for the fixed
+ *   scratch buffer") when one launch group of the four-step path needs more
+ *   than the array holds (FP32 N > 2^22, FP64 N > 2^21), or for an emulated plan.
+ */
+fst_status fst_project_noalloc(fst_plan_t plan, const void *y, void *out, int64_t batch,
+                               int64_t ld, int dtype, void *stream);
+unsigned long long fst_noalloc_scratch_bytes(void);
+
+/*
  * Launch accounting, for benchmarks (not part of the method).
  * fst_launch_count   -- number of kernels this process has launched through the
  *                       library so far (plan-time and apply kernels).

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -355,6 +356,51 @@ Runner *make_dev_runner() {
 using namespace fst;
 
 extern "C" long long fst_launch_count(void) { return g_launches; }
+
+// ---------------------------------------------------------------------------
+// fst_project_noalloc: fst_project for callers that cannot allocate device
+// memory at call time (for example code running inside a CUDA-graph capture or
+// under an allocator that forbids cudaMalloc/cudaFree after start-up).  The
+// four-step path's scratch (intermediate spectra, per-tile partial sums and the
+// correction coefficients) lives in one fixed file-scope device array instead of
+// the plan's on-demand workspace.  Every device that loads this library holds the
+// array until the process exits.
+// ---------------------------------------------------------------------------
+#define FST_NOALLOC_SCRATCH_BYTES (128ull << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FST_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" fst_status fst_project_noalloc(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld,
+                                          int dtype, void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (!p->R->device()) return fail(FST_EINVAL, "fst_project_noalloc needs a device plan");
+  int dev = 0;
+  CU(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(FST_EUNSUPPORTED, "device ordinal out of range");
+  void *scratch = nullptr;
+  {
+    // one-time set-up per device (with that device current): the host-side name of
+    // the array is only a stand-in, its device address comes from the runtime
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void *a = nullptr;
+      CU(cudaGetSymbolAddress(&a, g_noalloc_scratch), "cudaGetSymbolAddress");
+      g_scratch_addr[dev] = a;
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  p->R->set_stream(stream);
+  // nothing in the scratch has to start at zero: every kernel writes the part it
+  // later reads before reading it
+  return run_apply_ws(p, y, out, batch, ld, dtype, true, scratch, (size_t)FST_NOALLOC_SCRATCH_BYTES);
+}
+
+extern "C" unsigned long long fst_noalloc_scratch_bytes(void) { return FST_NOALLOC_SCRATCH_BYTES; }
 
 extern "C" fst_status fst_profile_enable(int on) {
   for (auto &r : g_prof) {

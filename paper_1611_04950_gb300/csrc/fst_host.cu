@@ -150,7 +150,8 @@ static fst_status ensure_ws(fst_plan_t p, size_t bytes) {
 
 template <typename T>
 static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64_t ld, bool cplx, bool full,
-                          const T *spec, const T *ST, const T *D, const Layout &L) {
+                          const T *spec, const T *ST, const T *D, const Layout &L0, void *ext_ws,
+                          size_t ext_bytes) {
   ConvArgs<T> a{};
   a.y = y;
   a.out = out;
@@ -166,11 +167,29 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.tw = plan_tw<T>(p);
   a.mode = full ? MODE_FULL : MODE_CONV;
   const int64_t npairs = cplx ? batch : (batch + 1) / 2;
-  TRY(ensure_ws(p, ws_need(L, sizeof(T) == 8, (int)p->rpad, false)));
-  return run_conv<T>(p->R, L, a, npairs, p->ws);
+  const bool dbl = sizeof(T) == 8;
+  if (!ext_ws) {
+    TRY(ensure_ws(p, ws_need(L0, dbl, (int)p->rpad, false)));
+    return run_conv<T>(p->R, L0, a, npairs, p->ws);
+  }
+  // caller-provided scratch: shrink the launch group until it fits
+  Layout L = L0;
+  if (!L.small) {
+    int64_t ch = L.chunk;
+    while (ch > L.G) {
+      L.chunk = ch;
+      if (ws_need(L, dbl, (int)p->rpad, false) <= ext_bytes) break;
+      ch = std::max<int64_t>(L.G, ((ch / 2) / L.G) * L.G);
+    }
+    L.chunk = ch;
+    if (ws_need(L, dbl, (int)p->rpad, false) > ext_bytes)
+      return fail(FST_EINVAL, "signal too long for the fixed scratch buffer");
+  }
+  return run_conv<T>(p->R, L, a, npairs, ext_ws);
 }
 
-fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full) {
+fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full,
+                        void *ws, size_t ws_bytes) {
   if (!p) return fail(FST_EINVAL, "plan is NULL");
   if (batch < 0) return fail(FST_EINVAL, "batch < 0");
   if (batch == 0) return FST_OK;
@@ -180,19 +199,23 @@ fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int6
   switch (dtype) {
     case FST_F32:
       return apply_t<float>(p, (const float *)y, (float *)out, batch, ld, false, full, p->spec32, p->ST32, p->D32,
-                            p->lay32);
+                            p->lay32, ws, ws_bytes);
     case FST_C64:
       return apply_t<float>(p, (const float *)y, (float *)out, batch, ld, true, full, p->spec32, p->ST32, p->D32,
-                            p->lay32);
+                            p->lay32, ws, ws_bytes);
     case FST_F64:
       return apply_t<double>(p, (const double *)y, (double *)out, batch, ld, false, full, p->spec64, p->ST64,
-                             p->D64, p->lay64);
+                             p->D64, p->lay64, ws, ws_bytes);
     case FST_C128:
       return apply_t<double>(p, (const double *)y, (double *)out, batch, ld, true, full, p->spec64, p->ST64,
-                             p->D64, p->lay64);
+                             p->D64, p->lay64, ws, ws_bytes);
     default:
       return fail(FST_EINVAL, "unknown dtype");
   }
+}
+
+fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full) {
+  return run_apply_ws(p, y, out, batch, ld, dtype, full, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -107,5 +107,9 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
                       double alpha);
 // B y (+ correction when full) for `batch` signals in runner memory
 fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full);
+// as run_apply with caller-provided scratch `ws` of ws_bytes (nullptr: the plan's own,
+// allocated on demand); with caller scratch nothing is allocated
+fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full,
+                        void *ws, size_t ws_bytes);
 void destroy_plan(fst_plan_t p);
 }  // namespace fst

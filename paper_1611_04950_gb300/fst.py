@@ -32,7 +32,8 @@ _STATUS = {0: "FST_OK", 1: "FST_EINVAL", 2: "FST_ENOMEM", 3: "FST_ECUDA", 4: "FS
 EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_project",
             "fst_project_host", "fst_apply_prolate", "fst_destroy", "fst_last_error", "fst_version",
             "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
-            "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read"]
+            "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
+            "fst_project_noalloc", "fst_noalloc_scratch_bytes"]
 
 
 class FSTError(RuntimeError):
@@ -61,6 +62,8 @@ def _load():
         "fst_emu_plan_op": ([C.POINTER(P), i64, d, i64, d, I, d], I),
         "fst_plan_is_emulated": ([P], I),
         "fst_launch_count": ([], C.c_longlong),
+        "fst_project_noalloc": ([P, vp, vp, i64, i64, I, vp], I),
+        "fst_noalloc_scratch_bytes": ([], C.c_ulonglong),
         "fst_profile_enable": ([I], I),
         "fst_profile_count": ([], I),
         "fst_profile_read": ([I, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)], I),
@@ -142,6 +145,16 @@ def fst_apply_prolate(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dty
 def fst_project_host(h: int, y_ptr: int, out_ptr: int, batch: int, dtype: int, stream: int = 0):
     _check(_lib.fst_project_host(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, dtype,
                                  C.c_void_p(stream)))
+
+
+def fst_project_noalloc(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dtype: int, stream: int = 0):
+    """fst_project without any device allocation (fixed library-owned scratch)."""
+    _check(_lib.fst_project_noalloc(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, ld, dtype,
+                                    C.c_void_p(stream)))
+
+
+def fst_noalloc_scratch_bytes() -> int:
+    return int(_lib.fst_noalloc_scratch_bytes())
 
 
 def fst_destroy(h: int):
