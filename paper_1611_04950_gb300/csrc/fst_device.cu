@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fst_internal.h"
+#include "fst_fast.cuh"
 
 namespace fst {
 
@@ -137,6 +138,14 @@ __global__ void k_gather(const double *S, int64_t N, const int *sel, int r, int 
     const double v = (j < r) ? S[(int64_t)sel[j] * N + n] : 0.0;
     ST64[t] = v;
     ST32[t] = (float)v;
+  }
+}
+
+__global__ void k_split_tf32(const float *src, float *hi, float *lo, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const float h = tf32_round(src[t]);
+    hi[t] = h;
+    lo[t] = tf32_round(src[t] - h);
   }
 }
 
@@ -287,13 +296,39 @@ struct DevRunner : Runner {
   }
   fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
-  fst_status passA(const ConvArgs<float> &a, const Layout &L) override { return passA_t(a, L); }
+  fst_status passA(const ConvArgs<float> &a, const Layout &L) override {
+    if (!L.fast) return passA_t(a, L);
+    FastArgs f{a, a.ST_hi, a.ST_lo};
+    dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
+    const int P = 1 << L.log2P;
+    if (P == 32) PROF("k_fastA<32>", a.npairs, (k_fastA<32><<<grid, FAST_THREADS, 0, s>>>(f)));
+    else if (P == 16) PROF("k_fastA<16>", a.npairs, (k_fastA<16><<<grid, FAST_THREADS, 0, s>>>(f)));
+    else PROF("k_fastA<8>", a.npairs, (k_fastA<8><<<grid, FAST_THREADS, 0, s>>>(f)));
+    LAUNCHED("k_fastA");
+    return FST_OK;
+  }
   fst_status passA(const ConvArgs<double> &a, const Layout &L) override { return passA_t(a, L); }
   fst_status reduce(const ConvArgs<float> &a, const Layout &L) override { return reduce_t(a, L); }
   fst_status reduce(const ConvArgs<double> &a, const Layout &L) override { return reduce_t(a, L); }
-  fst_status passB(const ConvArgs<float> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status passB(const ConvArgs<float> &a, const Layout &L) override {
+    if (!L.fast || L.log2Q != 12) return passB_t(a, L);
+    dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
+    PROF("k_fastB4096", a.npairs, (k_fastB4096<<<grid, 256, 0, s>>>(a)));
+    LAUNCHED("k_fastB4096");
+    return FST_OK;
+  }
   fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
-  fst_status passC(const ConvArgs<float> &a, const Layout &L) override { return passC_t(a, L); }
+  fst_status passC(const ConvArgs<float> &a, const Layout &L) override {
+    if (!L.fast) return passC_t(a, L);
+    FastArgs f{a, a.ST_hi, a.ST_lo};
+    dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
+    const int P = 1 << L.log2P;
+    if (P == 32) PROF("k_fastC<32>", a.npairs, (k_fastC<32><<<grid, FAST_THREADS, 0, s>>>(f)));
+    else if (P == 16) PROF("k_fastC<16>", a.npairs, (k_fastC<16><<<grid, FAST_THREADS, 0, s>>>(f)));
+    else PROF("k_fastC<8>", a.npairs, (k_fastC<8><<<grid, FAST_THREADS, 0, s>>>(f)));
+    LAUNCHED("k_fastC");
+    return FST_OK;
+  }
   fst_status passC(const ConvArgs<double> &a, const Layout &L) override { return passC_t(a, L); }
 
   fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
@@ -333,6 +368,11 @@ struct DevRunner : Runner {
                        float *ST32) override {
     k_gather<<<grid_for(N * rpad, 256), 256, 0, s>>>(S, N, sel, r, rpad, ST64, ST32);
     LAUNCHED("k_gather");
+    return FST_OK;
+  }
+  fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
+    k_split_tf32<<<grid_for(n, 256), 256, 0, s>>>(src, hi, lo, n);
+    LAUNCHED("k_split_tf32");
     return FST_OK;
   }
   fst_status to_f32(const double *src, float *dst, int64_t n) override {

@@ -161,6 +161,13 @@ struct EmuRunner : Runner {
     for (int64_t i = 0; i < n; ++i) dst[i] = (float)src[i];
     return FST_OK;
   }
+  fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
+    for (int64_t i = 0; i < n; ++i) {
+      hi[i] = tf32_round(src[i]);
+      lo[i] = tf32_round(src[i] - hi[i]);
+    }
+    return FST_OK;
+  }
 };
 
 Runner *make_emu_runner() { return new EmuRunner(); }

@@ -1,0 +1,418 @@
+// fst_fast.cuh -- FP32 four-step kernels for P = 8, 16, 32 column rows (device only).
+//
+// Same algorithm and data layout as the generic passA/passB/passC bodies of
+// fst_kernels.cuh (n = n1 Q + n2, k = k1 + P k2, inter[pair][k1][n2]), restructured
+// for the GB300 memory system:
+//   * column passes: one thread owns one whole column (all P rows of one n2 of one
+//     pair) in registers, so the P-point DFT needs no shared memory and every
+//     global access is coalesced across the 32 columns of a warp;
+//   * the rank-r correction runs on the tensor cores: per CTA tile (8 pairs = 16
+//     real signals x 32 columns x Pnz rows) the partial sums S_T^T y and the
+//     epilogue S_T a are small matrix products done with mma.sync m16n8k8 TF32,
+//     each operand split as hi + lo (both TF32) and three products kept
+//     (hi*hi + hi*lo + lo*hi), which keeps FP32-level accuracy;
+//   * row pass: the first radix-16 stage reads straight from global memory, the
+//     forward transform's last stage, the spectrum multiply and the inverse
+//     transform's first stage stay in registers, and the last stage writes straight
+//     to global memory (4 shared-memory round trips per row instead of 8).
+#pragma once
+#include "fst_kernels.cuh"
+
+namespace fst {
+
+constexpr int FAST_G = 8;      // pairs per column tile
+constexpr int FAST_NB = 32;    // columns (n2 values) per pair per tile
+constexpr int FAST_THREADS = FAST_G * FAST_NB;   // one thread per column
+constexpr int YT_STRIDE = 516; // padded row stride (floats) of the signal-major tile
+
+struct FastArgs {
+  ConvArgs<float> a;
+  const float *ST_hi;   // [N][rpad] TF32-rounded S_T
+  const float *ST_lo;   // [N][rpad] TF32(S_T - ST_hi)
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+// D += A(16x8, row) * B(8x8, col), TF32 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, const uint32_t *b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma3(float *d, const uint32_t *ahi, const uint32_t *alo, const uint32_t *bhi,
+                                     const uint32_t *blo) {
+  mma_tf32(d, alo, bhi);
+  mma_tf32(d, ahi, blo);
+  mma_tf32(d, ahi, bhi);
+}
+
+// In-register DFT of length P (8, 16 or 32) in natural order, unnormalised.
+template <int P, bool INV> struct RegDft;
+template <bool INV> struct RegDft<8, INV> {
+  __device__ __forceinline__ static void run(float2 *v) { Dft<float, 8, INV>::run(v); }
+};
+template <bool INV> struct RegDft<16, INV> {
+  __device__ __forceinline__ static void run(float2 *v) { Dft<float, 16, INV>::run(v); }
+};
+template <bool INV> struct RegDft<32, INV> {
+  // 32 = 16 x 2: Y_b = DFT16 over a of x[2a + b]; Y_1[c] *= W32^c; X[c + 16d] = Y_0[c] +- Y_1[c]
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) { e[a] = v[2 * a]; o[a] = v[2 * a + 1]; }
+    Dft<float, 16, INV>::run(e);
+    Dft<float, 16, INV>::run(o);
+    constexpr double C[8] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                             0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                             0.19509032201612826785};
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      // W32^c = cos(2 pi c/32) - i sin(2 pi c/32)
+      const int cc = c & 7;
+      float cr, si;
+      if (c < 8) { cr = (float)C[cc]; si = (float)C[(8 - cc) & 7]; if (cc == 0) si = 0.f; }
+      else { cr = -(float)C[(8 - cc) & 7]; si = (float)C[cc]; if (cc == 0) cr = 0.f; }
+      if (c == 8) { cr = 0.f; si = 1.f; }
+      const float2 w = make_float2(cr, INV ? si : -si);
+      const float2 t = (c == 0) ? o[c] : cmul(o[c], w);
+      v[c] = cadd(e[c], t);
+      v[c + 16] = csub(e[c], t);
+    }
+  }
+};
+
+// twiddles w^k, k = 0..P-1, of the root w = exp(-+2 pi i n2 / M): table lookups for
+// w and w^16 (and w^8 for P = 8 / 16), powers by at most three products
+template <int P, bool INV>
+__device__ __forceinline__ void twiddle_powers(const Tw<float> &tw, uint64_t n2, int log2M, float2 *w) {
+  w[0] = make_float2(1.f, 0.f);
+  w[1] = tw.template root<INV>(n2, log2M);
+  w[2] = cmul(w[1], w[1]);
+  w[3] = cmul(w[2], w[1]);
+  if (P > 4) {
+    w[4] = cmul(w[2], w[2]);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+  }
+  if (P > 8) {
+    w[8] = tw.template root<INV>(8 * n2, log2M);
+#pragma unroll
+    for (int b = 1; b < 8; ++b) w[8 + b] = cmul(w[8], w[b]);
+  }
+  if (P > 16) {
+    const float2 w16 = tw.template root<INV>(16 * n2, log2M);
+    w[16] = w16;
+#pragma unroll
+    for (int b = 1; b < 16; ++b) w[16 + b] = cmul(w16, w[b]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass A: load columns, correction partials (tensor cores), P-point DFT, twiddle
+// grid (ntiles, ngroups), FAST_THREADS threads; thread = (pair g = warp, column c = lane)
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(FAST_THREADS) k_fastA(const FastArgs f) {
+  const ConvArgs<float> &a = f.a;
+  __shared__ __align__(16) float yt[2 * FAST_G * YT_STRIDE];   // [signal][n_local], n_local = n1 * 32 + c
+  __shared__ float red[FAST_G][2 * FAST_G][8 * 3 + 1];         // per-warp partial C^T blocks
+  const int Q = 1 << a.log2Q;
+  const int g = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
+  const int64_t n2 = tile * FAST_NB + c;
+  const bool live = (g0 + g) < a.npairs;
+  const bool corr = a.mode == MODE_FULL && a.r > 0;
+
+  float2 v[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) v[i] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int n1 = 0; n1 < P / 2; ++n1) {
+    const int64_t n = (int64_t)n1 * Q + n2;
+    if (live && n1 < a.Pnz && n < a.N) v[n1] = load_pair(a, g0 + g, n);
+    if (corr) {
+      yt[(2 * g) * YT_STRIDE + n1 * 32 + c] = v[n1].x;
+      yt[(2 * g + 1) * YT_STRIDE + n1 * 32 + c] = v[n1].y;
+    }
+  }
+
+  if (corr) {
+    __syncthreads();
+    // C^T (16 signals x rpad) = Y^T (16 x nel) * S (nel x rpad); warp w takes the
+    // k-slice n_local in [w * nk, (w+1) * nk); the j range in n-tiles of 8
+    const int lane = c, gid = lane >> 2, tig = lane & 3;
+    const int nel = (P / 2) * 32;
+    const int nk = nel / FAST_G;            // k per warp (multiple of 8)
+    const int ntj = a.rpad / 8;             // j tiles of 8 (rpad multiple of 8)
+    for (int jt0 = 0; jt0 < ntj; jt0 += 3) {
+      float acc[3][4];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+      for (int k0 = g * nk; k0 < (g + 1) * nk; k0 += 8) {
+        uint32_t ahi[4], alo[4];
+        split_tf32(yt[gid * YT_STRIDE + k0 + tig], ahi[0], alo[0]);
+        split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig], ahi[1], alo[1]);
+        split_tf32(yt[gid * YT_STRIDE + k0 + tig + 4], ahi[2], alo[2]);
+        split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig + 4], ahi[3], alo[3]);
+        // rows of S for n_local = k0 + tig and k0 + tig + 4
+        const int nl0 = k0 + tig, nl1 = k0 + tig + 4;
+        const int64_t nA = (int64_t)(nl0 >> 5) * Q + tile * FAST_NB + (nl0 & 31);
+        const int64_t nB = (int64_t)(nl1 >> 5) * Q + tile * FAST_NB + (nl1 & 31);
+        const bool okA = nA < a.N, okB = nB < a.N;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int jt = jt0 + t;
+          if (jt < ntj) {
+            const int j = jt * 8 + gid;
+            uint32_t bhi[2], blo[2];
+            bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
+            blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
+            bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
+            blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
+            mma3(acc[t], ahi, alo, bhi, blo);
+          }
+        }
+      }
+      // acc[t]: rows (signals) gid, gid+8; cols (j) 2 tig, 2 tig + 1 of tile jt0 + t
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        red[g][gid][t * 8 + 2 * tig] = acc[t][0];
+        red[g][gid][t * 8 + 2 * tig + 1] = acc[t][1];
+        red[g][gid + 8][t * 8 + 2 * tig] = acc[t][2];
+        red[g][gid + 8][t * 8 + 2 * tig + 1] = acc[t][3];
+      }
+      __syncthreads();
+      // sum over the 8 warps in a fixed order: thread -> (signal s, column jj)
+      for (int t = threadIdx.x; t < 2 * FAST_G * 24; t += FAST_THREADS) {
+        const int s = t / 24, jj = t % 24;
+        const int j = jt0 * 8 + jj;
+        const int gp = s >> 1;
+        if (j < a.r && g0 + gp < a.npairs) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < FAST_G; ++w) sum += red[w][s][jj];
+          const int ntiles = Q / FAST_NB;
+          a.part[(((g0 + gp) * ntiles + tile) * 2 + (s & 1)) * a.rpad + j] = sum;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  if (!live) return;
+  RegDft<P, false>::run(v);
+  float2 w[P];
+  twiddle_powers<P, false>(a.tw, (uint64_t)n2, a.log2M, w);
+  float2 *dst = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) dst[(int64_t)k1 * Q] = (k1 == 0) ? v[0] : cmul(v[k1], w[k1]);
+}
+
+// ---------------------------------------------------------------------------
+// pass B for Q = 4096 = 16^3 (256 threads, 16 values per thread)
+// grid (P, npairs)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tw_stage16(const Tw<float> &tw, int k, int log2NsR, bool inv, float2 *x) {
+  // multiply x[t] by W_{Ns 16}^{k t}, t = 1..15
+  const uint32_t base = (uint32_t)k << (TW_LOG2 - log2NsR);
+  float2 w1 = inv ? tw.get<true>(base) : tw.get<false>(base);
+  float2 w4 = inv ? tw.get<true>(4 * base) : tw.get<false>(4 * base);
+  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+  const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
+  const float2 ws[4] = {make_float2(1.f, 0.f), w1, w2, w3};
+  const float2 wb[4] = {make_float2(1.f, 0.f), w4, w8, w12};
+#pragma unroll
+  for (int t = 1; t < 16; ++t) {
+    const int lo = t & 3, hi = t >> 2;
+    float2 wt = (lo == 0) ? wb[hi] : (hi == 0 ? ws[lo] : cmul(wb[hi], ws[lo]));
+    x[t] = cmul(x[t], wt);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
+  constexpr int Q = 4096, T = 256;
+  __shared__ float2 buf[padded_size(Q)];
+  const int P = 1 << a.log2P;
+  const int k1 = blockIdx.x;
+  const int64_t pl = blockIdx.y;
+  float2 *row = a.inter + (pl * P + k1) * (int64_t)Q;
+  const int j = threadIdx.x;
+  float2 x[16];
+  // forward stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = row[j + T * t];
+  Dft<float, 16, false>::run(x);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
+  __syncthreads();
+  // stage 2 (Ns = 16)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_stage16(a.tw, j & 15, 8, false, x);
+  Dft<float, 16, false>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
+  __syncthreads();
+  // stage 3 (Ns = 256): outputs land at j + 256 t = natural k2
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_stage16(a.tw, j, 12, false, x);
+  Dft<float, 16, false>::run(x);
+  if (a.mode == MODE_FORWARD) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) row[j + T * t] = x[t];
+    return;
+  }
+  const float *sp = a.spec + (int64_t)k1 * Q;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = cscale(x[t], __ldg(sp + j + T * t));
+  // inverse stage 1: its inputs x[j + 256 t] are already in registers
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_stage16(a.tw, j & 15, 8, true, x);
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_stage16(a.tw, j, 12, true, x);
+  Dft<float, 16, true>::run(x);
+  // times W_M^{-n2 k1}, n2 = j + 256 t, straight to global memory
+  const float2 wj = a.tw.root<true>((uint64_t)j * (uint64_t)k1, a.log2M);
+  const float2 wstep = a.tw.root<true>((uint64_t)T * (uint64_t)k1, a.log2M);
+  float2 wt = wj;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    row[j + T * t] = cmul(x[t], wt);
+    if (t == 7) wt = cmul(wj, a.tw.root<true>((uint64_t)(8 * T) * (uint64_t)k1, a.log2M));
+    else wt = cmul(wt, wstep);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass C: load columns, inverse P-point DFT, correction epilogue (tensor cores), store
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(FAST_THREADS) k_fastC(const FastArgs f) {
+  const ConvArgs<float> &a = f.a;
+  __shared__ __align__(16) float zt[(P / 2) * 32][2 * FAST_G + 1];   // Z tile [n_local][signal]
+  __shared__ float acs[2][32][2 * FAST_G + 1];                        // a (hi, lo) [j][signal]
+  const int Q = 1 << a.log2Q;
+  const int g = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
+  const int64_t n2 = tile * FAST_NB + c;
+  const bool live = (g0 + g) < a.npairs;
+  const bool corr = a.mode == MODE_FULL && a.r > 0;
+
+  float2 v[P];
+  if (live) {
+    const float2 *src = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) v[k1] = src[(int64_t)k1 * Q];
+    RegDft<P, true>::run(v);
+  }
+
+  if (corr) {
+    const int lane = c, gid = lane >> 2, tig = lane & 3;
+    const int nel = (P / 2) * 32;
+    const int ntj = a.rpad / 8;
+    for (int jt0 = 0; jt0 < ntj; jt0 += 4) {
+      // a (coefficients D o c) for j in [8 jt0, 8 jt0 + 32), all 16 signals, split hi/lo
+      for (int t = threadIdx.x; t < 32 * 2 * FAST_G; t += FAST_THREADS) {
+        const int jj = t / (2 * FAST_G), s = t % (2 * FAST_G);
+        const int j = jt0 * 8 + jj, gp = s >> 1;
+        float val = 0.f;
+        if (j < a.r && g0 + gp < a.npairs) val = a.acoef[((g0 + gp) * 2 + (s & 1)) * a.rpad + j];
+        uint32_t hi, lo;
+        split_tf32(val, hi, lo);
+        acs[0][jj][s] = __uint_as_float(hi);
+        acs[1][jj][s] = __uint_as_float(lo);
+      }
+      __syncthreads();
+      // Z (nel x 16) = S (nel x 32 j) * A (32 j x 16); warp w takes m-tiles of 16 rows
+      for (int mt = g; mt < nel / 16; mt += FAST_G) {
+        float acc[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+        const int nl0 = mt * 16 + gid, nl1 = nl0 + 8;
+        const int64_t nA = (int64_t)(nl0 >> 5) * Q + tile * FAST_NB + (nl0 & 31);
+        const int64_t nB = (int64_t)(nl1 >> 5) * Q + tile * FAST_NB + (nl1 & 31);
+        const bool okA = nA < a.N, okB = nB < a.N;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+          const int jt = jt0 + kt;
+          if (jt < ntj) {
+            const int j0 = jt * 8 + tig, j1 = j0 + 4;
+            uint32_t ahi[4], alo[4];
+            ahi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j0)) : 0u;
+            ahi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j0)) : 0u;
+            ahi[2] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j1)) : 0u;
+            ahi[3] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j1)) : 0u;
+            alo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j0)) : 0u;
+            alo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j0)) : 0u;
+            alo[2] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j1)) : 0u;
+            alo[3] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j1)) : 0u;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              // B (8 j x 8 signals): b0 = A[j = kt*8 + tig][s = u*8 + gid], b1 = A[j + 4][s]
+              uint32_t bhi[2], blo[2];
+              bhi[0] = __float_as_uint(acs[0][kt * 8 + tig][u * 8 + gid]);
+              bhi[1] = __float_as_uint(acs[0][kt * 8 + tig + 4][u * 8 + gid]);
+              blo[0] = __float_as_uint(acs[1][kt * 8 + tig][u * 8 + gid]);
+              blo[1] = __float_as_uint(acs[1][kt * 8 + tig + 4][u * 8 + gid]);
+              mma3(acc[u], ahi, alo, bhi, blo);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float add0 = (jt0 == 0) ? 0.f : zt[nl0][u * 8 + 2 * tig];
+          const float add1 = (jt0 == 0) ? 0.f : zt[nl0][u * 8 + 2 * tig + 1];
+          const float add2 = (jt0 == 0) ? 0.f : zt[nl1][u * 8 + 2 * tig];
+          const float add3 = (jt0 == 0) ? 0.f : zt[nl1][u * 8 + 2 * tig + 1];
+          zt[nl0][u * 8 + 2 * tig] = add0 + acc[u][0];
+          zt[nl0][u * 8 + 2 * tig + 1] = add1 + acc[u][1];
+          zt[nl1][u * 8 + 2 * tig] = add2 + acc[u][2];
+          zt[nl1][u * 8 + 2 * tig + 1] = add3 + acc[u][3];
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  if (!live) return;
+  float *outp = a.out;
+#pragma unroll
+  for (int n1 = 0; n1 < P / 2; ++n1) {
+    const int64_t n = (int64_t)n1 * Q + n2;
+    if (n1 < a.Pnz && n < a.N) {
+      float2 val = v[n1];
+      if (corr) {
+        val.x += zt[n1 * 32 + c][2 * g];
+        val.y += zt[n1 * 32 + c][2 * g + 1];
+      }
+      store_pair(a, g0 + g, n, val);
+    }
+  }
+  (void)outp;
+}
+
+}  // namespace fst

@@ -45,7 +45,7 @@ static int64_t chunk_bytes_target() {
   return mb << 20;
 }
 
-Layout make_layout(int64_t N, int log2M, bool dbl, int rpad) {
+Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast) {
   Layout L;
   const size_t cs = dbl ? 16 : 8;   // bytes per complex
   const size_t rs = dbl ? 8 : 4;    // bytes per real
@@ -68,19 +68,29 @@ Layout make_layout(int64_t N, int log2M, bool dbl, int rpad) {
   L.log2Q = std::min(qmax, std::max(qmin, log2M - 5));
   L.log2P = log2M - L.log2Q;
   const int P = 1 << L.log2P, Q = 1 << L.log2Q;
-  const int tile = 8192;
-  const int ncols = std::max(1, tile / P);
-  const int nb0 = std::min(32, ncols);
-  L.G = std::min(ncols / nb0, 16);
-  L.NB = ncols / L.G;
-  L.ntiles = Q / L.NB;
   L.Pnz = (int)((N + Q - 1) / Q);
-  L.nthr_A = L.nthr_C = std::max(32, ncols * P / 16);
   L.nthr_B = std::max(32, Q / 16);
-  const int nwarps = L.nthr_A / 32;
-  L.smem_A = padded_size(P * ncols) * cs + (size_t)nwarps * 128 * rs;
-  L.smem_C = padded_size(P * ncols) * cs;
   L.smem_B = padded_size(Q) * cs;
+  if (allow_fast && !dbl && P >= 8 && P <= 32) {
+    // register column passes: 8 pairs x 32 columns per CTA, one thread per column
+    L.fast = true;
+    L.G = 8;
+    L.NB = 32;
+    L.ntiles = Q / L.NB;
+    L.nthr_A = L.nthr_C = 256;
+    L.smem_A = L.smem_C = 0;
+  } else {
+    const int tile = 8192;
+    const int ncols = std::max(1, tile / P);
+    const int nb0 = std::min(32, ncols);
+    L.G = std::min(ncols / nb0, 16);
+    L.NB = ncols / L.G;
+    L.ntiles = Q / L.NB;
+    L.nthr_A = L.nthr_C = std::max(32, ncols * P / 16);
+    const int nwarps = L.nthr_A / 32;
+    L.smem_A = padded_size(P * ncols) * cs + (size_t)nwarps * 128 * rs;
+    L.smem_C = padded_size(P * ncols) * cs;
+  }
   int64_t ch = chunk_bytes_target() / (int64_t)(M * cs);
   ch = std::max<int64_t>(L.G, (ch / L.G) * L.G);
   L.chunk = ch;
@@ -161,6 +171,10 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.N = p->N;
   a.spec = spec;
   a.ST = ST;
+  if (sizeof(T) == 4) {
+    a.ST_hi = (const T *)p->ST32_hi;
+    a.ST_lo = (const T *)p->ST32_lo;
+  }
   a.r = full ? (int)p->r : 0;
   a.rpad = (int)p->rpad;
   a.D = D;
@@ -547,7 +561,7 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     }
   }
   p->r = (int64_t)sel.size();
-  p->rpad = std::max<int64_t>(4, (p->r + 3) / 4 * 4);
+  p->rpad = std::max<int64_t>(8, (p->r + 7) / 8 * 8);
   {
     fst_status s;
     const size_t nst = (size_t)N * p->rpad;
@@ -567,10 +581,13 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
       if ((s = R->zero(p->ST32, nst * sizeof(float))) != FST_OK) return bail(s);
     }
     if ((s = R->to_f32(p->D64, p->D32, p->rpad)) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->ST32_hi, nst * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->ST32_lo, nst * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->split_tf32(p->ST32, p->ST32_hi, p->ST32_lo, (int64_t)nst)) != FST_OK) return bail(s);
     if ((s = R->sync()) != FST_OK) return bail(s);
   }
-  p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad);
-  p->lay64 = make_layout(N, p->log2M, true, (int)p->rpad);
+  p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad, R->device());
+  p->lay64 = make_layout(N, p->log2M, true, (int)p->rpad, false);
   if (p->lay32.small && p->lay32.smem_small > 227 * 1024)
     return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
   if (p->lay64.small && p->lay64.smem_small > 227 * 1024)
@@ -584,7 +601,7 @@ void destroy_plan(fst_plan_t p) {
   Runner *R = p->R;
   if (R) {
     R->sync();
-    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64,
+    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hi, p->ST32_lo,
                     p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);

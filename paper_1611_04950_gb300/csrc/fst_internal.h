@@ -21,6 +21,7 @@ namespace fst {
 // Launch layout of the length-M transform for one real type.
 struct Layout {
   bool small = true;
+  bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
   int log2M = 0, log2P = 0, log2Q = 0;
   int Pnz = 0, NB = 0, G = 1, ntiles = 0;
   int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
@@ -28,7 +29,7 @@ struct Layout {
   int64_t chunk = 1;   // pairs per launch group
 };
 
-Layout make_layout(int64_t N, int log2M, bool dbl, int rpad);
+Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast = false);
 // position of natural frequency index k in the layout's spectrum array
 __host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
   if (L.small) return k;
@@ -74,6 +75,7 @@ struct Runner {
   virtual fst_status gather_ST(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64,
                                float *ST32) = 0;
   virtual fst_status to_f32(const double *src, float *dst, int64_t n) = 0;
+  virtual fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) = 0;
 };
 
 Runner *make_dev_runner();
@@ -88,7 +90,7 @@ struct fst_plan_s {
   double W = 0, eps = 0, alpha = 0, beta = 1;
   int op = 0;
   fst::Layout lay32, lay64;
-  float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr;
+  float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr, *ST32_hi = nullptr, *ST32_lo = nullptr;
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
   float2 *tw32h = nullptr, *tw32l = nullptr;
   double2 *tw64h = nullptr, *tw64l = nullptr;

@@ -53,6 +53,8 @@ template <typename T> struct ConvArgs {
   // plan data
   const T *spec;      // DFT_M(c) * beta / M, natural order (small) or [k1][k2] (3-pass)
   const T *ST;        // [N][rpad], row n = (s_j[n])_j, zero padded
+  const T *ST_hi;     // FP32 fast path: TF32-rounded S_T and the TF32 remainder
+  const T *ST_lo;
   int r, rpad;
   const T *D;         // [r]
   Tw<T> tw;
@@ -62,6 +64,15 @@ template <typename T> struct ConvArgs {
   T *acoef;           // [npairs][2][rpad]: D o c for (re, im)
   int mode;
 };
+
+// TF32 rounding (round to nearest, ties away from zero, 10 mantissa bits kept)
+FST_HD float tf32_round(float x) {
+  union { float f; uint32_t u; } v;
+  v.f = x;
+  if ((v.u & 0x7f800000u) == 0x7f800000u) return x;
+  v.u = (v.u + 0x1000u) & 0xffffe000u;
+  return v.f;
+}
 
 template <typename T> struct KState {
   c2<T> v[16];
