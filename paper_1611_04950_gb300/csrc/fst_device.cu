@@ -213,10 +213,12 @@ static void prof_end(cudaStream_t s, cudaEvent_t ea) {
 #define PROF(name, units, launch)            \
   do {                                       \
     cudaEvent_t _ea;                         \
-    prof_begin(s, name, (units), &_ea);      \
+    prof_begin(cur, name, (units), &_ea);    \
     launch;                                  \
-    prof_end(s, _ea);                        \
+    prof_end(cur, _ea);                      \
   } while (0)
+
+bool profiling_enabled() { return g_prof_on != 0; }
 
 static inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
@@ -224,10 +226,80 @@ static inline int grid_for(int64_t n, int block) {
 }
 
 struct DevRunner : Runner {
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;     // caller's stream
+  cudaStream_t cur = nullptr;   // stream the apply kernels go to (s, or a capture lane)
+  cudaStream_t cap[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool capturing = false;
+  long long launches_at_begin = 0;
   bool device() const override { return true; }
-  void set_stream(void *st) override { s = (cudaStream_t)st; }
+  void set_stream(void *st) override { s = (cudaStream_t)st; cur = s; }
   void *stream() const override { return (void *)s; }
+  ~DevRunner() override {
+    for (int i = 0; i < 2; ++i)
+      if (cap[i]) cudaStreamDestroy(cap[i]);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+  }
+
+  int lanes() const override { return capturing ? 2 : 1; }
+  void use_lane(int i) override { cur = capturing ? cap[i & 1] : s; }
+  bool user_stream_capturing() override {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+      cudaGetLastError();
+      return true;
+    }
+    return st != cudaStreamCaptureStatusNone;
+  }
+  bool graph_begin() override {
+    if (!cap[0]) {
+      for (int i = 0; i < 2; ++i)
+        if (cudaStreamCreateWithFlags(&cap[i], cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return false; }
+      if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+    }
+    if (set_attrs() != FST_OK) return false;
+    if (cudaStreamBeginCapture(cap[0], cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaEventRecord(fork, cap[0]);
+    cudaStreamWaitEvent(cap[1], fork, 0);
+    capturing = true;
+    cur = cap[0];
+    launches_at_begin = g_launches;
+    return true;
+  }
+  fst_status graph_end(void **exec, long long *nodes) override {
+    *exec = nullptr;
+    cudaEventRecord(join, cap[1]);
+    cudaStreamWaitEvent(cap[0], join, 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap[0], &g);
+    capturing = false;
+    cur = s;
+    *nodes = g_launches - launches_at_begin;
+    g_launches = launches_at_begin;   // captured, not yet run
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    *exec = (void *)ex;
+    return FST_OK;
+  }
+  fst_status graph_launch(void *exec, long long nodes) override {
+    CU(cudaGraphLaunch((cudaGraphExec_t)exec, s), "cudaGraphLaunch");
+    g_launches += nodes;
+    return FST_OK;
+  }
+  void graph_destroy(void *exec) override {
+    if (exec) cudaGraphExecDestroy((cudaGraphExec_t)exec);
+  }
 
   fst_status alloc(void **p, size_t bytes) override {
     *p = nullptr;
@@ -263,34 +335,34 @@ struct DevRunner : Runner {
   template <typename T> fst_status small_t(const ConvArgs<T> &a, const Layout &L) {
     if (set_attrs() != FST_OK) return FST_ECUDA;
     PROF(sizeof(T) == 4 ? "k_small<f32>" : "k_small<f64>", a.npairs,
-         (k_small<T><<<(unsigned)a.npairs, L.nthr_small, L.smem_small, s>>>(a)));
+         (k_small<T><<<(unsigned)a.npairs, L.nthr_small, L.smem_small, cur>>>(a)));
     LAUNCHED("k_small");
     return FST_OK;
   }
   template <typename T> fst_status passA_t(const ConvArgs<T> &a, const Layout &L) {
     if (set_attrs() != FST_OK) return FST_ECUDA;
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + L.G - 1) / L.G));
-    PROF(sizeof(T) == 4 ? "k_passA<f32>" : "k_passA<f64>", a.npairs, (k_passA<T><<<grid, L.nthr_A, L.smem_A, s>>>(a)));
+    PROF(sizeof(T) == 4 ? "k_passA<f32>" : "k_passA<f64>", a.npairs, (k_passA<T><<<grid, L.nthr_A, L.smem_A, cur>>>(a)));
     LAUNCHED("k_passA");
     return FST_OK;
   }
   template <typename T> fst_status reduce_t(const ConvArgs<T> &a, const Layout &) {
     const int thr = std::min(1024, std::max(32, ((2 * a.r + 31) / 32) * 32));
-    PROF(sizeof(T) == 4 ? "k_reduce<f32>" : "k_reduce<f64>", a.npairs, (k_reduce<T><<<(unsigned)a.npairs, thr, 0, s>>>(a)));
+    PROF(sizeof(T) == 4 ? "k_reduce<f32>" : "k_reduce<f64>", a.npairs, (k_reduce<T><<<(unsigned)a.npairs, thr, 0, cur>>>(a)));
     LAUNCHED("k_reduce");
     return FST_OK;
   }
   template <typename T> fst_status passB_t(const ConvArgs<T> &a, const Layout &L) {
     if (set_attrs() != FST_OK) return FST_ECUDA;
     dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
-    PROF(sizeof(T) == 4 ? "k_passB<f32>" : "k_passB<f64>", a.npairs, (k_passB<T><<<grid, L.nthr_B, L.smem_B, s>>>(a)));
+    PROF(sizeof(T) == 4 ? "k_passB<f32>" : "k_passB<f64>", a.npairs, (k_passB<T><<<grid, L.nthr_B, L.smem_B, cur>>>(a)));
     LAUNCHED("k_passB");
     return FST_OK;
   }
   template <typename T> fst_status passC_t(const ConvArgs<T> &a, const Layout &L) {
     if (set_attrs() != FST_OK) return FST_ECUDA;
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + L.G - 1) / L.G));
-    PROF(sizeof(T) == 4 ? "k_passC<f32>" : "k_passC<f64>", a.npairs, (k_passC<T><<<grid, L.nthr_C, L.smem_C, s>>>(a)));
+    PROF(sizeof(T) == 4 ? "k_passC<f32>" : "k_passC<f64>", a.npairs, (k_passC<T><<<grid, L.nthr_C, L.smem_C, cur>>>(a)));
     LAUNCHED("k_passC");
     return FST_OK;
   }
@@ -301,9 +373,9 @@ struct DevRunner : Runner {
     FastArgs f{a, a.ST_hi, a.ST_lo};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     const int P = 1 << L.log2P;
-    if (P == 32) PROF("k_fastA<32>", a.npairs, (k_fastA<32><<<grid, FAST_THREADS, 0, s>>>(f)));
-    else if (P == 16) PROF("k_fastA<16>", a.npairs, (k_fastA<16><<<grid, FAST_THREADS, 0, s>>>(f)));
-    else PROF("k_fastA<8>", a.npairs, (k_fastA<8><<<grid, FAST_THREADS, 0, s>>>(f)));
+    if (P == 32) PROF("k_fastA<32>", a.npairs, (k_fastA<32><<<grid, FAST_THREADS, 0, cur>>>(f)));
+    else if (P == 16) PROF("k_fastA<16>", a.npairs, (k_fastA<16><<<grid, FAST_THREADS, 0, cur>>>(f)));
+    else PROF("k_fastA<8>", a.npairs, (k_fastA<8><<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_fastA");
     return FST_OK;
   }
@@ -313,7 +385,7 @@ struct DevRunner : Runner {
   fst_status passB(const ConvArgs<float> &a, const Layout &L) override {
     if (!L.fast || L.log2Q != 12) return passB_t(a, L);
     dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
-    PROF("k_fastB4096", a.npairs, (k_fastB4096<<<grid, 256, 0, s>>>(a)));
+    PROF("k_fastB4096", a.npairs, (k_fastB4096<<<grid, 256, 0, cur>>>(a)));
     LAUNCHED("k_fastB4096");
     return FST_OK;
   }
@@ -323,9 +395,9 @@ struct DevRunner : Runner {
     FastArgs f{a, a.ST_hi, a.ST_lo};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     const int P = 1 << L.log2P;
-    if (P == 32) PROF("k_fastC<32>", a.npairs, (k_fastC<32><<<grid, FAST_THREADS, 0, s>>>(f)));
-    else if (P == 16) PROF("k_fastC<16>", a.npairs, (k_fastC<16><<<grid, FAST_THREADS, 0, s>>>(f)));
-    else PROF("k_fastC<8>", a.npairs, (k_fastC<8><<<grid, FAST_THREADS, 0, s>>>(f)));
+    if (P == 32) PROF("k_fastC<32>", a.npairs, (k_fastC<32><<<grid, FAST_THREADS, 0, cur>>>(f)));
+    else if (P == 16) PROF("k_fastC<16>", a.npairs, (k_fastC<16><<<grid, FAST_THREADS, 0, cur>>>(f)));
+    else PROF("k_fastC<8>", a.npairs, (k_fastC<8><<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_fastC");
     return FST_OK;
   }

@@ -90,39 +90,12 @@ template <bool INV> struct RegDft<32, INV> {
   }
 };
 
-// twiddles w^k, k = 0..P-1, of the root w = exp(-+2 pi i n2 / M): table lookups for
-// w and w^16 (and w^8 for P = 8 / 16), powers by at most three products
-template <int P, bool INV>
-__device__ __forceinline__ void twiddle_powers(const Tw<float> &tw, uint64_t n2, int log2M, float2 *w) {
-  w[0] = make_float2(1.f, 0.f);
-  w[1] = tw.template root<INV>(n2, log2M);
-  w[2] = cmul(w[1], w[1]);
-  w[3] = cmul(w[2], w[1]);
-  if (P > 4) {
-    w[4] = cmul(w[2], w[2]);
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-  }
-  if (P > 8) {
-    w[8] = tw.template root<INV>(8 * n2, log2M);
-#pragma unroll
-    for (int b = 1; b < 8; ++b) w[8 + b] = cmul(w[8], w[b]);
-  }
-  if (P > 16) {
-    const float2 w16 = tw.template root<INV>(16 * n2, log2M);
-    w[16] = w16;
-#pragma unroll
-    for (int b = 1; b < 16; ++b) w[16 + b] = cmul(w16, w[b]);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // pass A: load columns, correction partials (tensor cores), P-point DFT, twiddle
 // grid (ntiles, ngroups), FAST_THREADS threads; thread = (pair g = warp, column c = lane)
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(FAST_THREADS) k_fastA(const FastArgs f) {
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_fastA(const FastArgs f) {
   const ConvArgs<float> &a = f.a;
   __shared__ __align__(16) float yt[2 * FAST_G * YT_STRIDE];   // [signal][n_local], n_local = n1 * 32 + c
   __shared__ float red[FAST_G][2 * FAST_G][8 * 3 + 1];         // per-warp partial C^T blocks
@@ -146,6 +119,33 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastA(const FastArgs f) {
     }
   }
 
+  if (live) {
+  RegDft<P, false>::run(v);
+  // times W_M^{n2 k1}: k1 = 8h + b, W^{k1} = W^{8h} W^b; table lookups for W, W^8, W^16,
+  // small powers by at most two products, applied and stored right away
+  float2 *dst = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
+  const float2 w1 = a.tw.root<false>((uint64_t)n2, a.log2M);
+  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
+  float2 wh[4];
+  wh[0] = make_float2(1.f, 0.f);
+  if (P > 8) wh[1] = a.tw.root<false>(8 * (uint64_t)n2, a.log2M);
+  if (P > 16) {
+    wh[2] = a.tw.root<false>(16 * (uint64_t)n2, a.log2M);
+    wh[3] = cmul(wh[2], wh[1]);
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int l = b & 3;
+    float2 wb = (l == 0) ? make_float2(1.f, 0.f) : (l == 1 ? w1 : (l == 2 ? w2 : w3));
+    if (b >= 4) wb = (l == 0) ? w4 : cmul(w4, wb);
+#pragma unroll
+    for (int h = 0; h < P / 8; ++h) {
+      const int k1 = 8 * h + b;
+      const float2 w = (h == 0) ? wb : (b == 0 ? wh[h] : cmul(wh[h], wb));
+      dst[(int64_t)k1 * Q] = (k1 == 0) ? v[0] : cmul(v[k1], w);
+    }
+  }
+  }
   if (corr) {
     __syncthreads();
     // C^T (16 signals x rpad) = Y^T (16 x nel) * S (nel x rpad); warp w takes the
@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastA(const FastArgs f) {
       float acc[3][4];
 #pragma unroll
       for (int t = 0; t < 3; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-      for (int k0 = g * nk; k0 < (g + 1) * nk; k0 += 8) {
+#pragma unroll
+      for (int ks = 0; ks < P / 4; ++ks) {   // nk / 8 = P / 4 k-steps per warp
+        const int k0 = g * nk + ks * 8;
         uint32_t ahi[4], alo[4];
         split_tf32(yt[gid * YT_STRIDE + k0 + tig], ahi[0], alo[0]);
         split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig], ahi[1], alo[1]);
@@ -209,13 +211,6 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastA(const FastArgs f) {
     }
   }
 
-  if (!live) return;
-  RegDft<P, false>::run(v);
-  float2 w[P];
-  twiddle_powers<P, false>(a.tw, (uint64_t)n2, a.log2M, w);
-  float2 *dst = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
-#pragma unroll
-  for (int k1 = 0; k1 < P; ++k1) dst[(int64_t)k1 * Q] = (k1 == 0) ? v[0] : cmul(v[k1], w[k1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -247,6 +242,16 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
   const int64_t pl = blockIdx.y;
   float2 *row = a.inter + (pl * P + k1) * (int64_t)Q;
   const int j = threadIdx.x;
+  if (k1 == 0 && a.mode == MODE_FULL && a.r > 0) {
+    // a = D o (sum of the column-tile partials of S_T^T y), fixed order
+    const int ntiles = Q / FAST_NB;
+    for (int t = j; t < 2 * a.r; t += T) {
+      const int c = t / a.r, jj = t % a.r;
+      float sum = 0.f;
+      for (int tile = 0; tile < ntiles; ++tile) sum += a.part[((pl * ntiles + tile) * 2 + c) * a.rpad + jj];
+      a.acoef[(pl * 2 + c) * a.rpad + jj] = __ldg(a.D + jj) * sum;
+    }
+  }
   float2 x[16];
   // forward stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory
 #pragma unroll
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
 // pass C: load columns, inverse P-point DFT, correction epilogue (tensor cores), store
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(FAST_THREADS) k_fastC(const FastArgs f) {
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
   const ConvArgs<float> &a = f.a;
   __shared__ __align__(16) float zt[(P / 2) * 32][2 * FAST_G + 1];   // Z tile [n_local][signal]
   __shared__ float acs[2][32][2 * FAST_G + 1];                        // a (hi, lo) [j][signal]
@@ -321,14 +326,6 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastC(const FastArgs f) {
   const int64_t n2 = tile * FAST_NB + c;
   const bool live = (g0 + g) < a.npairs;
   const bool corr = a.mode == MODE_FULL && a.r > 0;
-
-  float2 v[P];
-  if (live) {
-    const float2 *src = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
-#pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) v[k1] = src[(int64_t)k1 * Q];
-    RegDft<P, true>::run(v);
-  }
 
   if (corr) {
     const int lane = c, gid = lane >> 2, tig = lane & 3;
@@ -348,7 +345,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastC(const FastArgs f) {
       }
       __syncthreads();
       // Z (nel x 16) = S (nel x 32 j) * A (32 j x 16); warp w takes m-tiles of 16 rows
-      for (int mt = g; mt < nel / 16; mt += FAST_G) {
+#pragma unroll
+      for (int mi = 0; mi < P / 8; ++mi) {
+        const int mt = g + FAST_G * mi;
         float acc[2][4];
 #pragma unroll
         for (int u = 0; u < 2; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
@@ -399,6 +398,13 @@ __global__ void __launch_bounds__(FAST_THREADS) k_fastC(const FastArgs f) {
   }
 
   if (!live) return;
+  float2 v[P];
+  {
+    const float2 *src = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) v[k1] = src[(int64_t)k1 * Q];
+    RegDft<P, true>::run(v);
+  }
   float *outp = a.out;
 #pragma unroll
   for (int n1 = 0; n1 < P / 2; ++n1) {

@@ -40,7 +40,7 @@ static int ilog2_exact(int64_t x) {
 
 static int64_t chunk_bytes_target() {
   const char *s = getenv("FST_CHUNK_MB");
-  int64_t mb = s ? atoll(s) : 64;
+  int64_t mb = s ? atoll(s) : 128;
   if (mb < 1) mb = 1;
   return mb << 20;
 }
@@ -79,6 +79,7 @@ Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast) {
     L.ntiles = Q / L.NB;
     L.nthr_A = L.nthr_C = 256;
     L.smem_A = L.smem_C = 0;
+    L.fused_reduce = (L.log2Q == 12);
   } else {
     const int tile = 8192;
     const int ncols = std::max(1, tile / P);
@@ -111,6 +112,9 @@ static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
 // convolution driver
 // ---------------------------------------------------------------------------
 
+// bytes of one launch group's scratch (one lane)
+static size_t slot_bytes(const Layout &L, bool dbl, int rpad, bool forward) { return ws_need(L, dbl, rpad, forward); }
+
 template <typename T>
 static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t npairs, void *ws) {
   using C = c2<T>;
@@ -122,25 +126,31 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   a.G = L.G;
   if (a.mode == MODE_FORWARD && !L.small) a.Pnz = 1 << L.log2P;
   const int64_t M = 1LL << L.log2M;
-  char *w = (char *)ws;
-  a.inter = (C *)w;
-  if (!L.small) {
-    const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
-    a.part = (T *)(w + inter_b);
-    a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
-  }
-  for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk) {
+  const int lanes = R->lanes();
+  const size_t slot = slot_bytes(L, sizeof(T) == 8, a.rpad, a.mode == MODE_FORWARD);
+  int64_t group = 0;
+  for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk, ++group) {
+    const int lane = (int)(group % lanes);
+    R->use_lane(lane);
+    char *w = (char *)ws + (size_t)lane * slot;
+    a.inter = (C *)w;
+    if (!L.small) {
+      const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
+      a.part = (T *)(w + inter_b);
+      a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
+    }
     a.pair0 = p0;
     a.npairs = std::min<int64_t>(L.chunk, npairs - p0);
     if (L.small) {
       TRY(R->small(a, L));
     } else {
       TRY(R->passA(a, L));
-      if (a.mode == MODE_FULL && a.r > 0) TRY(R->reduce(a, L));
+      if (a.mode == MODE_FULL && a.r > 0 && !(L.fused_reduce && R->device())) TRY(R->reduce(a, L));
       TRY(R->passB(a, L));
       if (a.mode != MODE_FORWARD) TRY(R->passC(a, L));
     }
   }
+  R->use_lane(0);
   return FST_OK;
 }
 
@@ -148,8 +158,16 @@ template <typename T> static Tw<T> plan_tw(fst_plan_t p);
 template <> Tw<float> plan_tw<float>(fst_plan_t p) { return Tw<float>{p->tw32h, p->tw32l}; }
 template <> Tw<double> plan_tw<double>(fst_plan_t p) { return Tw<double>{p->tw64h, p->tw64l}; }
 
+static bool graphs_enabled() {
+  const char *s = getenv("FST_GRAPHS");
+  return !(s && s[0] == '0');
+}
+
 static fst_status ensure_ws(fst_plan_t p, size_t bytes) {
   if (bytes <= p->ws_bytes) return FST_OK;
+  // the cached graphs point at the old workspace
+  for (auto &e : p->graphs) p->R->graph_destroy(e.exec);
+  p->graphs.clear();
   if (p->ws) p->R->release(p->ws);
   p->ws = nullptr;
   p->ws_bytes = 0;
@@ -183,8 +201,38 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   const int64_t npairs = cplx ? batch : (batch + 1) / 2;
   const bool dbl = sizeof(T) == 8;
   if (!ext_ws) {
-    TRY(ensure_ws(p, ws_need(L0, dbl, (int)p->rpad, false)));
-    return run_conv<T>(p->R, L0, a, npairs, p->ws);
+    Runner *R = p->R;
+    const size_t slot = ws_need(L0, dbl, (int)p->rpad, false);
+    const bool graphs = R->device() && graphs_enabled() && !profiling_enabled() && !R->user_stream_capturing();
+    if (!graphs) {
+      TRY(ensure_ws(p, slot));
+      return run_conv<T>(R, L0, a, npairs, p->ws);
+    }
+    // whole apply as one cached CUDA graph (two overlapping lanes of launch groups)
+    for (auto &e : p->graphs)
+      if (e.y == (const void *)y && e.out == (void *)out && e.batch == batch && e.ld == ld &&
+          e.dtype == (int)(cplx ? 1 : 0) + (dbl ? 2 : 0) && e.full == full)
+        return R->graph_launch(e.exec, e.nodes);
+    TRY(ensure_ws(p, 2 * slot + 256));
+    if (!R->graph_begin()) {
+      return run_conv<T>(R, L0, a, npairs, p->ws);
+    }
+    fst_status st = run_conv<T>(R, L0, a, npairs, p->ws);
+    void *exec = nullptr;
+    long long nodes = 0;
+    fst_status st2 = R->graph_end(&exec, &nodes);
+    if (st != FST_OK) {
+      if (exec) R->graph_destroy(exec);
+      return st;
+    }
+    TRY(st2);
+    if (p->graphs.size() >= 8) {
+      R->graph_destroy(p->graphs.front().exec);
+      p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back({(const void *)y, (void *)out, batch, ld, (int)(cplx ? 1 : 0) + (dbl ? 2 : 0), full, exec,
+                         nodes});
+    return R->graph_launch(exec, nodes);
   }
   // caller-provided scratch: shrink the launch group until it fits
   Layout L = L0;
@@ -601,6 +649,8 @@ void destroy_plan(fst_plan_t p) {
   Runner *R = p->R;
   if (R) {
     R->sync();
+    for (auto &e : p->graphs) R->graph_destroy(e.exec);
+    p->graphs.clear();
     void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hi, p->ST32_lo,
                     p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
     for (void *b : bufs)

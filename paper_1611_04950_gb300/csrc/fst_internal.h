@@ -22,6 +22,7 @@ namespace fst {
 struct Layout {
   bool small = true;
   bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
+  bool fused_reduce = false;  // the row pass also sums the correction partials (device fast path, Q = 4096)
   int log2M = 0, log2P = 0, log2Q = 0;
   int Pnz = 0, NB = 0, G = 1, ntiles = 0;
   int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
@@ -42,6 +43,16 @@ struct Runner {
   virtual bool device() const = 0;
   virtual void set_stream(void *) {}
   virtual void *stream() const { return nullptr; }
+  // CUDA-graph capture of a whole apply (device runner only).  While capturing,
+  // lanes() == 2 and use_lane(i) selects one of two capture streams, so that
+  // consecutive launch groups overlap.
+  virtual bool graph_begin() { return false; }
+  virtual fst_status graph_end(void **exec, long long *nodes) { return FST_EUNSUPPORTED; }
+  virtual fst_status graph_launch(void *exec, long long nodes) { return FST_EUNSUPPORTED; }
+  virtual void graph_destroy(void *exec) {}
+  virtual bool user_stream_capturing() { return false; }
+  virtual int lanes() const { return 1; }
+  virtual void use_lane(int) {}
   virtual fst_status alloc(void **p, size_t bytes) = 0;
   virtual void release(void *p) = 0;
   virtual fst_status h2d(void *dst, const void *src, size_t bytes) = 0;
@@ -99,6 +110,16 @@ struct fst_plan_s {
   std::vector<int64_t> idx;
   std::vector<double> lam, D;
   std::vector<double> lam_window;
+  struct GraphEntry {
+    const void *y;
+    void *out;
+    int64_t batch, ld;
+    int dtype;
+    bool full;
+    void *exec;
+    long long nodes;
+  };
+  std::vector<GraphEntry> graphs;   // cached whole-apply CUDA graphs (device plans)
 };
 
 namespace fst {
@@ -114,4 +135,5 @@ fst_status run_apply(fst_plan_t p, const void *y, void *out, int64_t batch, int6
 fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype, bool full,
                         void *ws, size_t ws_bytes);
 void destroy_plan(fst_plan_t p);
+bool profiling_enabled();   // per-launch event timing is on (fst_profile_enable)
 }  // namespace fst
