@@ -141,6 +141,45 @@ fst_status fst_project_host(fst_plan_t plan, const void *y, void *out, int64_t b
 fst_status fst_apply_prolate(fst_plan_t plan, const void *y, void *out, int64_t batch,
                              int64_t ld, int dtype, void *stream);
 
+/*
+ * fst_coeffs -- the fast coefficient vector c = T2^* y of the fast factorization
+ * S_K S_K^* ~ T1 T2^* (Section 1.3, "A fast factorization of S_K S_K^*"), with
+ * T2 = [F_{N,W}  L2  U2]: F_{N,W} the 2NW' lowest DFT vectors / sqrt(N)
+ * (Eq. PartialFourierMatrix; 2NW' the odd integer nearest 2NW, ties rounded up),
+ * L2 the right factor of Theorem 1's construction (Section 2: CF-ADI factor of the
+ * Hilbert matrix with the optimal shifts of the appendix, Taylor factors of A1 and
+ * B0, phase ramps D_A, D_B) and U2 = [sqrt(|D_l|) s_l] over the transition set.
+ * T1 c reproduces S_K S_K^* y within 2 eps ||y|| (Theorem 1 + Corollary 2).
+ *   y       device signals as for fst_project (N must be a power of two).
+ *   coeffs  device output, batch x K' complex values (complex64 for FST_F32 /
+ *           FST_C64 input, complex128 for FST_F64 / FST_C128), signal b at b*K'.
+ *           Per signal: F^* y for DFT bins k = -h..h (2h+1 = 2NW'), then the eight
+ *           L2 blocks in the order of the proof ((D_A J Z)^*y, (D_A Z)^*y,
+ *           (D_A^* J Z)^*y, (D_A^* Z)^*y, C_A V_A^T D_A^*y, C_A V_A^T D_A y,
+ *           C_B V_B^T D_B^*y, C_B V_B^T D_B y; V = centred monomials
+ *           ((n - (N-1)/2)/N)^i), then U2^* y.
+ * The first call builds the construction's tables (host FP64) and allocates.
+ * Errors: FST_EINVAL (NULL, batch < 0, ld < N, non-projection plan),
+ * FST_EUNSUPPORTED (N not a power of two), FST_ENOMEM, FST_ECUDA.
+ */
+fst_status fst_coeffs(fst_plan_t plan, const void *y, void *coeffs, int64_t batch, int64_t ld,
+                      int dtype, void *stream);
+
+/*
+ * fst_coeffs_info -- sizes of the coefficient vector (any pointer may be NULL):
+ * K' = 2NW' + r1 + r, nF = 2NW', r1 = 4 r_H + 4 r_A + 2 (2 r_B - 1) and the ranks
+ * r_H, r_A, r_B of Section 2.  Builds the construction's tables on first use.
+ */
+fst_status fst_coeffs_info(fst_plan_t plan, int64_t *Kprime, int64_t *nF, int64_t *r1,
+                           int64_t *rH, int64_t *rA, int64_t *rB);
+
+/*
+ * fst_adi_shifts -- HOST helper: the r optimal CF-ADI shifts for A = diag(n + 1/2),
+ * n < N (appendix, last remarks): p_k = b dn((2k-1)/(2r) K(m), m), b = N - 1/2,
+ * m = 1 - (1/(2N-1))^2, computed by the arithmetic-geometric mean.  out[r].
+ */
+fst_status fst_adi_shifts(int64_t N, int r, double *out);
+
 /* fst_destroy -- frees the plan and its device memory.  NULL-safe. */
 fst_status fst_destroy(fst_plan_t plan);
 

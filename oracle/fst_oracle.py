@@ -179,9 +179,13 @@ def dpss_dense(N: int, W: float):
 
 
 def rayleigh_eigenvalues(S: np.ndarray, W: float, M: int | None = None) -> np.ndarray:
-    """lambda_l = s_l^T B s_l for each column (s_l unit norm eigenvectors of B)."""
-    BS = apply_prolate(S, W, M)
-    return np.einsum("ij,ij->j", S, BS)
+    """lambda_l = s_l^T B s_l for each column (s_l unit norm eigenvectors of B);
+    columns in groups of 8 to bound the FFT's memory at large N."""
+    lam = np.empty(S.shape[1])
+    for j0 in range(0, S.shape[1], 8):
+        blk = S[:, j0:j0 + 8]
+        lam[j0:j0 + 8] = np.einsum("ij,ij->j", blk, apply_prolate(blk, W, M))
+    return lam
 
 
 # ---------------------------------------------------------------------------

@@ -294,9 +294,10 @@ def T_factors(t: Thm1, plan: O.Plan):
 
 # --------------------------------------------------------------------------- matrix-free coefficients
 
-def coeffs(t: Thm1, plan: O.Plan, y: np.ndarray) -> np.ndarray:
+def coeffs(t: Thm1, plan: O.Plan | None, y: np.ndarray) -> np.ndarray:
     """T2^* y without forming T2 (any N).  y: (N,) or (N, batch), real or complex.
-    Order: F^* y (frequencies -h..h), then the eight L2 blocks, then U2^* y."""
+    Order: F^* y (frequencies -h..h), then the eight L2 blocks, then U2^* y
+    (left out when plan is None)."""
     y = np.asarray(y)
     one = y.ndim == 1
     Y = y[:, None] if one else y
@@ -334,9 +335,11 @@ def coeffs(t: Thm1, plan: O.Plan, y: np.ndarray) -> np.ndarray:
     b5, b6 = t.CA @ qA, t.CA @ qAc
     b7, b8 = t.CB @ qB, t.CB @ qBc
     cL = np.vstack([b1, b2, b3, b4, b5, b6, b7, b8])
-    _, U2 = U_factors(plan)
-    cU = U2.T @ Y
-    c = np.vstack([cF, cL, cU])
+    if plan is None:
+        c = np.vstack([cF, cL])
+    else:
+        _, U2 = U_factors(plan)
+        c = np.vstack([cF, cL, U2.T @ Y])
     return c[:, 0] if one else c
 
 

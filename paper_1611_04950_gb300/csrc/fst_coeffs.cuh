@@ -1,0 +1,292 @@
+// fst_coeffs.cuh -- kernel bodies of the fast coefficient vector T2^* y of the fast
+// factorization S_K S_K^* ~ T1 T2^* (Section 1.3; T2 = [F_{N,W}  L2  U2], L2 from the
+// constructive proof of Theorem 1 in Section 2, U2 from the proof of Corollary 2).
+//
+//   F^* y : the length-N DFT bins k = -h..h (2h+1 = 2NW') divided by sqrt(N), from the
+//           library's forward FFT (forward mode of the convolution kernels) + gather.
+//   L2^* y: eight blocks, every column a real weight times a phase ramp:
+//             (D_A J Z)^* y, (D_A Z)^* y, (D_A^* J Z)^* y, (D_A^* Z)^* y,
+//             C_A V_A^T D_A^* y, C_A V_A^T D_A y, C_B V_B^T D_B^* y, C_B V_B^T D_B y,
+//           with D_A = diag(exp(j 2 pi W' n)), D_B = diag(exp(j pi (W + W') n)),
+//           Z the CF-ADI factor of the Hilbert matrix (columns by the recurrence of
+//           the appendix, x = n + 1/2), V_A, V_B centred monomials u_n^i,
+//           u_n = (n - (N-1)/2)/N.  The kernel forms the sums over n (partials per
+//           n-chunk); the reduce kernel adds the chunks in a fixed order and applies
+//           C_A, C_B.
+//   U2^* y: sqrt|D_l| s_l^T y (partials per n-chunk, then a fixed-order reduce).
+#pragma once
+#include "fst_kernels.cuh"
+
+namespace fst {
+
+constexpr int COEF_THREADS = 256;
+constexpr int COEF_E = 8;      // samples per thread per chunk
+constexpr int COEF_CHUNK = COEF_THREADS * COEF_E;
+constexpr int COEF_GROUP = 8;  // complex outputs reduced per round
+
+template <typename T> struct CoefArgs {
+  const T *y;        // signals (real rows of N, or complex rows of N pairs)
+  int64_t ld, batch;
+  int cplx;
+  int64_t N;
+  int rH, DA, DB;    // ADI rank, 2 r_A, 2 r_B - 1
+  const T *zfirst;   // [rH]: zfirst[0] = sqrt(2 p_1); zfirst[k] = sqrt(p_{k+1}/p_k) (1-based p)
+  const T *zshift;   // [rH]: p_k (k = 1..rH), 1-based p stored at [k-1]
+  const c2<T> *phA;  // [N]: exp(-j 2 pi W' n)
+  const c2<T> *phB;  // [N]: exp(-j pi (W + W') n)
+  int nraw;          // raw outputs per signal: 4 rH + 2 DA + 2 DB
+  int nchunks;
+  T *part;           // [batch][nchunks][nraw][2]
+  // U2 part
+  const T *ST;       // [N][rpad]
+  int r, rpad;
+  T *partU;          // [batch][nchunks][r][2]
+};
+
+template <typename T> struct CState {
+  c2<T> v[COEF_E];   // phase-multiplied samples
+  T zf[COEF_E], zr[COEF_E], up[COEF_E];
+  T acc[2 * COEF_GROUP];
+};
+
+template <typename T> FST_HD c2<T> coef_sample(const CoefArgs<T> &a, int64_t sig, int64_t n) {
+  if (a.cplx) return reinterpret_cast<const c2<T> *>(a.y)[sig * a.ld + n];
+  return mk<T>(a.y[sig * a.ld + n], (T)0);
+}
+
+// Block-wide fixed-order reduction of every thread's acc[0 .. 2*cnt) into dst[0 .. 2*cnt):
+// red: nthr * 2 * COEF_GROUP reals of shared memory.
+template <typename T, typename Ex>
+FST_HD void coef_block_reduce(Ex &ex, T *red, int cnt, T *dst) {
+  using St = typename Ex::State;
+  const int nthr = ex.nthr;
+  ex.phase([&](int tid, St &st) {
+    for (int q = 0; q < 2 * cnt; ++q) red[q * nthr + tid] = st.acc[q];
+  });
+  ex.phase([&](int tid, St &) {
+    // thread (q, part): 8 parts of nthr / 8 values each, then the parts in order
+    const int parts = 8, span = nthr / parts;
+    if (tid < 2 * cnt * parts) {
+      const int q = tid / parts, pidx = tid % parts;
+      T s = 0;
+      for (int t = pidx * span; t < (pidx + 1) * span; ++t) s += red[q * nthr + t];
+      red[2 * COEF_GROUP * nthr + q * parts + pidx] = s;
+    }
+  });
+  ex.phase([&](int tid, St &) {
+    if (tid < 2 * cnt) {
+      T s = 0;
+      for (int pidx = 0; pidx < 8; ++pidx) s += red[2 * COEF_GROUP * nthr + tid * 8 + pidx];
+      dst[tid] = s;
+    }
+  });
+}
+
+// Raw low-rank sums of one signal over one chunk of samples.
+// Output order (complex): [b2 | b1 | qA-] for the D_A^* y variant, then
+// [b4 | b3 | qA+] for D_A y, then qB- (D_B^* y) and qB+ (D_B y), where
+// bZ = sum Z(n) v(n), bJ = sum Z(N-1-n) v(n), q[i] = sum u_n^i v(n).
+template <typename T, typename Ex>
+FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chunk, T *red) {
+  using St = typename Ex::State;
+  const int nthr = ex.nthr;
+  const int64_t n0 = (int64_t)chunk * COEF_CHUNK;
+  T *out = a.part + ((sig * a.nchunks + chunk) * a.nraw) * 2;
+  const T half = (T)0.5, Nd = (T)a.N, cen = (T)(0.5 * (double)(a.N - 1)), invN = (T)(1.0 / (double)a.N);
+  int obase = 0;
+  for (int variant = 0; variant < 4; ++variant) {
+    const bool useA = variant < 2, conjph = (variant & 1) != 0;
+    // v(n) = phase(n) y(n) with phase = exp(-j..) (conjph: exp(+j..)); reset recurrences
+    ex.phase([&](int tid, St &st) {
+      for (int e = 0; e < COEF_E; ++e) {
+        const int64_t n = n0 + tid + (int64_t)e * nthr;
+        c2<T> v = mk<T>(0, 0);
+        T zf = 0, zr = 0;
+        if (n < a.N) {
+          c2<T> ph = useA ? a.phA[n] : a.phB[n];
+          if (conjph) ph = cconj(ph);
+          v = cmul(ph, coef_sample(a, sig, n));
+          const T x = (T)n + half, xr = Nd - x;      // x for n and for N-1-n
+          zf = a.zfirst[0] / (x + a.zshift[0]);
+          zr = a.zfirst[0] / (xr + a.zshift[0]);
+        }
+        st.v[e] = v;
+        st.zf[e] = zf;
+        st.zr[e] = zr;
+        st.up[e] = (T)1;
+      }
+    });
+    if (useA) {
+      // Z columns, COEF_GROUP / 2 of them per round (two outputs each: Z and JZ)
+      for (int k0 = 0; k0 < a.rH; k0 += COEF_GROUP / 2) {
+        const int kc = (a.rH - k0 < COEF_GROUP / 2) ? a.rH - k0 : COEF_GROUP / 2;
+        ex.phase([&](int tid, St &st) {
+          for (int q = 0; q < 2 * COEF_GROUP; ++q) st.acc[q] = 0;
+          for (int kk = 0; kk < kc; ++kk) {
+            const int k = k0 + kk;
+            for (int e = 0; e < COEF_E; ++e) {
+              const int64_t n = n0 + tid + (int64_t)e * nthr;
+              if (k > 0 && n < a.N) {
+                const T x = (T)n + half, xr = Nd - x;
+                const T pk = a.zshift[k], pk1 = a.zshift[k - 1], sc = a.zfirst[k];
+                st.zf[e] = sc * (x - pk1) / (x + pk) * st.zf[e];
+                st.zr[e] = sc * (xr - pk1) / (xr + pk) * st.zr[e];
+              }
+              st.acc[4 * kk + 0] += st.zf[e] * st.v[e].x;
+              st.acc[4 * kk + 1] += st.zf[e] * st.v[e].y;
+              st.acc[4 * kk + 2] += st.zr[e] * st.v[e].x;
+              st.acc[4 * kk + 3] += st.zr[e] * st.v[e].y;
+            }
+          }
+        });
+        T res[2 * COEF_GROUP];
+        coef_block_reduce<T>(ex, red, 2 * kc, red + 2 * COEF_GROUP * nthr + 16 * 8);
+        ex.phase([&](int tid, St &) {
+          const T *r = red + 2 * COEF_GROUP * nthr + 16 * 8;
+          if (tid < kc) {
+            const int k = k0 + tid;
+            out[2 * (obase + k)] = r[4 * tid + 0];                 // sum Z v
+            out[2 * (obase + k) + 1] = r[4 * tid + 1];
+            out[2 * (obase + a.rH + k)] = r[4 * tid + 2];          // sum JZ v
+            out[2 * (obase + a.rH + k) + 1] = r[4 * tid + 3];
+          }
+        });
+        (void)res;
+      }
+      obase += 2 * a.rH;
+    }
+    // monomials u^i, i < D
+    const int D = useA ? a.DA : a.DB;
+    for (int i0 = 0; i0 < D; i0 += COEF_GROUP) {
+      const int ic = (D - i0 < COEF_GROUP) ? D - i0 : COEF_GROUP;
+      ex.phase([&](int tid, St &st) {
+        for (int q = 0; q < 2 * COEF_GROUP; ++q) st.acc[q] = 0;
+        for (int ii = 0; ii < ic; ++ii) {
+          for (int e = 0; e < COEF_E; ++e) {
+            const int64_t n = n0 + tid + (int64_t)e * nthr;
+            const T u = ((T)n - cen) * invN;
+            if (i0 + ii > 0) st.up[e] *= u;
+            st.acc[2 * ii] += st.up[e] * st.v[e].x;
+            st.acc[2 * ii + 1] += st.up[e] * st.v[e].y;
+          }
+        }
+      });
+      coef_block_reduce<T>(ex, red, ic, red + 2 * COEF_GROUP * nthr + 16 * 8);
+      ex.phase([&](int tid, St &) {
+        const T *r = red + 2 * COEF_GROUP * nthr + 16 * 8;
+        if (tid < ic) {
+          out[2 * (obase + i0 + tid)] = r[2 * tid];
+          out[2 * (obase + i0 + tid) + 1] = r[2 * tid + 1];
+        }
+      });
+    }
+    obase += D;
+  }
+}
+
+// S_T^T y partial sums of one signal over one chunk: warps split the samples, lanes
+// split j (j = lane + 32 q).  red: nwarps * 2 * 64 reals.
+template <typename T, typename Ex>
+FST_HD void coef_st_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chunk, T *red) {
+  using St = typename Ex::State;
+  const int nthr = ex.nthr, nwarps = nthr / 32;
+  const int64_t n0 = (int64_t)chunk * COEF_CHUNK;
+  const int64_t n1 = (n0 + COEF_CHUNK < a.N) ? n0 + COEF_CHUNK : a.N;
+  for (int j0 = 0; j0 < a.r; j0 += 64) {
+    ex.phase([&](int tid, St &) {
+      const int w = tid >> 5, lane = tid & 31;
+      T acc[4] = {0, 0, 0, 0};
+      const int ja = j0 + lane, jb = j0 + lane + 32;
+      for (int64_t n = n0 + w; n < n1; n += nwarps) {
+        const c2<T> v = coef_sample(a, sig, n);
+        const T *row = a.ST + n * a.rpad;
+        const T sa = (ja < a.r) ? ldg(row + ja) : (T)0;
+        const T sb = (jb < a.r) ? ldg(row + jb) : (T)0;
+        acc[0] += sa * v.x; acc[1] += sa * v.y;
+        acc[2] += sb * v.x; acc[3] += sb * v.y;
+      }
+      T *rw = red + w * 128;
+      rw[2 * lane] = acc[0]; rw[2 * lane + 1] = acc[1];
+      rw[64 + 2 * lane] = acc[2]; rw[64 + 2 * lane + 1] = acc[3];
+    });
+    ex.phase([&](int tid, St &) {
+      if (tid < 128) {
+        const int jj = tid >> 1, c = tid & 1;   // output j0 + jj, component c
+        T s = 0;
+        for (int w = 0; w < nwarps; ++w) s += red[w * 128 + 2 * jj + c];
+        const int j = j0 + jj;
+        if (j < a.r) a.partU[((sig * a.nchunks + chunk) * a.r + j) * 2 + c] = s;
+      }
+    });
+  }
+}
+
+// F^* y bins of signal `sig` for k = -h..h from the forward DFT X of its pair
+// (natural index kk stored at pos(kk) of the forward layout): real pairs split as
+// X_a = (Z[kk] + conj Z[-kk]) / 2, X_b = (Z[kk] - conj Z[-kk]) / (2j).
+template <typename T>
+FST_HD void coef_gather_body(const c2<T> *X, const Layout &Lf, int64_t N, int cplx, int64_t sig, int64_t pl,
+                             int64_t h, int64_t k, c2<T> *out) {
+  const int64_t kk = ((k - h) % N + N) % N;
+  const int64_t nk = (N - kk) % N;
+  const c2<T> *Xp = X + pl * N;
+  const c2<T> z = Xp[spec_pos(Lf, kk)];
+  c2<T> v;
+  if (cplx) {
+    v = z;
+  } else {
+    const c2<T> zc = cconj(Xp[spec_pos(Lf, nk)]);
+    if ((sig & 1) == 0) v = cscale(cadd(z, zc), (T)0.5);
+    else {
+      const c2<T> d = csub(z, zc);
+      v = mk<T>((T)0.5 * d.y, (T)(-0.5) * d.x);     // d / (2j)
+    }
+  }
+  const T s = (T)(1.0 / sqrt((double)N));
+  out[k] = cscale(v, s);
+}
+
+// totals[sig][o] = sum over chunks (fixed order) of part[sig][chunk][o]
+template <typename T>
+FST_HD void coef_reduce_body(const T *part, int nchunks, int nout, int64_t sig, int o, T *tot) {
+  T sr = 0, si = 0;
+  for (int c = 0; c < nchunks; ++c) {
+    const T *q = part + ((sig * nchunks + c) * (int64_t)nout + o) * 2;
+    sr += q[0];
+    si += q[1];
+  }
+  tot[(sig * (int64_t)nout + o) * 2] = sr;
+  tot[(sig * (int64_t)nout + o) * 2 + 1] = si;
+}
+
+// final L2^* y and U2^* y entries (index o in [0, r1 + r)) from the raw totals
+template <typename T>
+FST_HD c2<T> coef_mix_value(const CoefArgs<T> &a, const T *raw, const T *rawU, const T *CA, const T *CB,
+                            const T *sqrtD, int o) {
+  const int rH = a.rH, DA = a.DA, DB = a.DB;
+  auto R = [&](int i) { return mk<T>(raw[2 * i], raw[2 * i + 1]); };
+  const int r1 = 4 * rH + 2 * DA + 2 * DB;
+  if (o < rH) return R(rH + o);                                  // (D_A J Z)^* y
+  if (o < 2 * rH) return R(o - rH);                              // (D_A Z)^* y
+  if (o < 3 * rH) return R(2 * rH + DA + rH + (o - 2 * rH));     // (D_A^* J Z)^* y
+  if (o < 4 * rH) return R(2 * rH + DA + (o - 3 * rH));          // (D_A^* Z)^* y
+  if (o < r1) {
+    int base, D, i;
+    const T *C;
+    if (o < 4 * rH + DA) { i = o - 4 * rH; base = 2 * rH; D = DA; C = CA; }                     // C_A qA-
+    else if (o < 4 * rH + 2 * DA) { i = o - 4 * rH - DA; base = 4 * rH + DA; D = DA; C = CA; }   // C_A qA+
+    else if (o < 4 * rH + 2 * DA + DB) { i = o - 4 * rH - 2 * DA; base = 4 * rH + 2 * DA; D = DB; C = CB; }
+    else { i = o - 4 * rH - 2 * DA - DB; base = 4 * rH + 2 * DA + DB; D = DB; C = CB; }
+    T sr = 0, si = 0;
+    for (int l = 0; l < D; ++l) {
+      const T c = C[i * D + l];
+      sr += c * raw[2 * (base + l)];
+      si += c * raw[2 * (base + l) + 1];
+    }
+    return mk<T>(sr, si);
+  }
+  const int j = o - r1;
+  return mk<T>(sqrtD[j] * rawU[2 * j], sqrtD[j] * rawU[2 * j + 1]);
+}
+
+}  // namespace fst

@@ -42,6 +42,18 @@ struct DevExPlan {
   }
 };
 
+template <typename S> struct DevExS {
+  using State = S;
+  int nthr;
+  int tid;
+  State st;
+  __device__ DevExS() : nthr(blockDim.x), tid(threadIdx.x) {}
+  template <typename F> __device__ __forceinline__ void phase(F &&f) {
+    f(tid, st);
+    __syncthreads();
+  }
+};
+
 // ---------------------------------------------------------------------------
 // apply kernels
 // ---------------------------------------------------------------------------
@@ -139,6 +151,42 @@ __global__ void k_gather(const double *S, int64_t N, const int *sel, int r, int 
     ST64[t] = v;
     ST32[t] = (float)v;
   }
+}
+
+// ---- fast coefficient vector kernels ----
+template <typename T> __global__ void __launch_bounds__(COEF_THREADS) k_coef_lowrank(const CoefArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  DevExS<CState<T>> ex;
+  coef_lowrank_body<T>(ex, a, (int64_t)blockIdx.y, (int)blockIdx.x, reinterpret_cast<T *>(smem));
+}
+template <typename T> __global__ void __launch_bounds__(COEF_THREADS) k_coef_st(const CoefArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  DevExS<CState<T>> ex;
+  coef_st_body<T>(ex, a, (int64_t)blockIdx.y, (int)blockIdx.x, reinterpret_cast<T *>(smem));
+}
+template <typename T> __global__ void k_coef_reduce(const T *part, int nchunks, int nout, T *tot) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < nout) coef_reduce_body<T>(part, nchunks, nout, (int64_t)blockIdx.y, o, tot);
+}
+template <typename T>
+__global__ void k_coef_gather(const c2<T> *X, Layout Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig, int64_t h,
+                              c2<T> *out, int64_t Kp) {
+  const int64_t nF = 2 * h + 1, total = nsig * nF;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = sig0 + t / nF, k = t % nF;
+    const int64_t pl = cplx ? (s - sig0) : (s / 2 - sig0 / 2);
+    coef_gather_body<T>(X, Lf, N, cplx, s, pl, h, k, out + s * Kp);
+  }
+}
+template <typename T>
+__global__ void k_coef_mix(const CoefArgs<T> a, const T *tot, const T *totU, const T *CA, const T *CB, const T *sq,
+                           c2<T> *out, int64_t Kp, int64_t nF) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sig = blockIdx.y;
+  const int nfin = 4 * a.rH + 2 * a.DA + 2 * a.DB + a.r;
+  if (o >= nfin) return;
+  out[sig * Kp + nF + o] =
+      coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2, totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o);
 }
 
 __global__ void k_split_tf32(const float *src, float *hi, float *lo, int64_t n) {
@@ -442,6 +490,74 @@ struct DevRunner : Runner {
     LAUNCHED("k_gather");
     return FST_OK;
   }
+  template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
+    const size_t smem = (2 * COEF_GROUP * COEF_THREADS + 16 * 8 + 16) * sizeof(T);
+    dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
+    k_coef_lowrank<T><<<grid, COEF_THREADS, smem, s>>>(a);
+    LAUNCHED("k_coef_lowrank");
+    ++g_launches;
+    return FST_OK;
+  }
+  template <typename T> fst_status coef_st_t(const CoefArgs<T> &a) {
+    const size_t smem = (COEF_THREADS / 32) * 128 * sizeof(T);
+    dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
+    k_coef_st<T><<<grid, COEF_THREADS, smem, s>>>(a);
+    LAUNCHED("k_coef_st");
+    ++g_launches;
+    return FST_OK;
+  }
+  template <typename T> fst_status coef_reduce_t(const T *part, int nchunks, int nout, int64_t batch, T *tot) {
+    dim3 grid((unsigned)((nout + 127) / 128), (unsigned)batch);
+    k_coef_reduce<T><<<grid, 128, 0, s>>>(part, nchunks, nout, tot);
+    LAUNCHED("k_coef_reduce");
+    ++g_launches;
+    return FST_OK;
+  }
+  template <typename T>
+  fst_status coef_gather_t(const c2<T> *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                           int64_t h, c2<T> *out, int64_t Kp) {
+    k_coef_gather<T><<<grid_for(nsig * (2 * h + 1), 256), 256, 0, s>>>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+    LAUNCHED("k_coef_gather");
+    ++g_launches;
+    return FST_OK;
+  }
+  template <typename T>
+  fst_status coef_mix_t(const CoefArgs<T> &a, const T *tot, const T *totU, const T *CA, const T *CB, const T *sq,
+                        c2<T> *out, int64_t Kp, int64_t nF) {
+    const int nfin = 4 * a.rH + 2 * a.DA + 2 * a.DB + a.r;
+    dim3 grid((unsigned)((nfin + 127) / 128), (unsigned)a.batch);
+    k_coef_mix<T><<<grid, 128, 0, s>>>(a, tot, totU, CA, CB, sq, out, Kp, nF);
+    LAUNCHED("k_coef_mix");
+    ++g_launches;
+    return FST_OK;
+  }
+  fst_status coef_lowrank(const CoefArgs<float> &a) override { return coef_lowrank_t(a); }
+  fst_status coef_lowrank(const CoefArgs<double> &a) override { return coef_lowrank_t(a); }
+  fst_status coef_st(const CoefArgs<float> &a) override { return coef_st_t(a); }
+  fst_status coef_st(const CoefArgs<double> &a) override { return coef_st_t(a); }
+  fst_status coef_reduce(const float *part, int nchunks, int nout, int64_t batch, float *tot) override {
+    return coef_reduce_t(part, nchunks, nout, batch, tot);
+  }
+  fst_status coef_reduce(const double *part, int nchunks, int nout, int64_t batch, double *tot) override {
+    return coef_reduce_t(part, nchunks, nout, batch, tot);
+  }
+  fst_status coef_gather(const float2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                         int64_t h, float2 *out, int64_t Kp) override {
+    return coef_gather_t<float>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+  }
+  fst_status coef_gather(const double2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                         int64_t h, double2 *out, int64_t Kp) override {
+    return coef_gather_t<double>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+  }
+  fst_status coef_mix(const CoefArgs<float> &a, const float *tot, const float *totU, const float *CA, const float *CB,
+                      const float *sq, float2 *out, int64_t Kp, int64_t nF) override {
+    return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
+  }
+  fst_status coef_mix(const CoefArgs<double> &a, const double *tot, const double *totU, const double *CA,
+                      const double *CB, const double *sq, double2 *out, int64_t Kp, int64_t nF) override {
+    return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
+  }
+
   fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
     k_split_tf32<<<grid_for(n, 256), 256, 0, s>>>(src, hi, lo, n);
     LAUNCHED("k_split_tf32");

@@ -161,6 +161,76 @@ struct EmuRunner : Runner {
     for (int64_t i = 0; i < n; ++i) dst[i] = (float)src[i];
     return FST_OK;
   }
+  template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
+    std::vector<T> red(2 * COEF_GROUP * COEF_THREADS + 16 * 8 + 16);
+    for (int64_t sig = 0; sig < a.batch; ++sig)
+      for (int c = 0; c < a.nchunks; ++c) {
+        HostEx<CState<T>> ex(COEF_THREADS);
+        coef_lowrank_body<T>(ex, a, sig, c, red.data());
+      }
+    return FST_OK;
+  }
+  template <typename T> fst_status coef_st_t(const CoefArgs<T> &a) {
+    std::vector<T> red((COEF_THREADS / 32) * 128);
+    for (int64_t sig = 0; sig < a.batch; ++sig)
+      for (int c = 0; c < a.nchunks; ++c) {
+        HostEx<CState<T>> ex(COEF_THREADS);
+        coef_st_body<T>(ex, a, sig, c, red.data());
+      }
+    return FST_OK;
+  }
+  template <typename T> fst_status coef_reduce_t(const T *part, int nchunks, int nout, int64_t batch, T *tot) {
+    for (int64_t sig = 0; sig < batch; ++sig)
+      for (int o = 0; o < nout; ++o) coef_reduce_body<T>(part, nchunks, nout, sig, o, tot);
+    return FST_OK;
+  }
+  template <typename T>
+  fst_status coef_gather_t(const c2<T> *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                           int64_t h, c2<T> *out, int64_t Kp) {
+    for (int64_t s = sig0; s < sig0 + nsig; ++s)
+      for (int64_t k = 0; k < 2 * h + 1; ++k) {
+        const int64_t pl = cplx ? (s - sig0) : (s / 2 - sig0 / 2);
+        coef_gather_body<T>(X, Lf, N, cplx, s, pl, h, k, out + s * Kp);
+      }
+    return FST_OK;
+  }
+  template <typename T>
+  fst_status coef_mix_t(const CoefArgs<T> &a, const T *tot, const T *totU, const T *CA, const T *CB, const T *sq,
+                        c2<T> *out, int64_t Kp, int64_t nF) {
+    const int nfin = 4 * a.rH + 2 * a.DA + 2 * a.DB + a.r;
+    for (int64_t sig = 0; sig < a.batch; ++sig)
+      for (int o = 0; o < nfin; ++o)
+        out[sig * Kp + nF + o] = coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2,
+                                                    totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o);
+    return FST_OK;
+  }
+  fst_status coef_lowrank(const CoefArgs<float> &a) override { return coef_lowrank_t(a); }
+  fst_status coef_lowrank(const CoefArgs<double> &a) override { return coef_lowrank_t(a); }
+  fst_status coef_st(const CoefArgs<float> &a) override { return coef_st_t(a); }
+  fst_status coef_st(const CoefArgs<double> &a) override { return coef_st_t(a); }
+  fst_status coef_reduce(const float *part, int nchunks, int nout, int64_t batch, float *tot) override {
+    return coef_reduce_t(part, nchunks, nout, batch, tot);
+  }
+  fst_status coef_reduce(const double *part, int nchunks, int nout, int64_t batch, double *tot) override {
+    return coef_reduce_t(part, nchunks, nout, batch, tot);
+  }
+  fst_status coef_gather(const float2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                         int64_t h, float2 *out, int64_t Kp) override {
+    return coef_gather_t<float>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+  }
+  fst_status coef_gather(const double2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
+                         int64_t h, double2 *out, int64_t Kp) override {
+    return coef_gather_t<double>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+  }
+  fst_status coef_mix(const CoefArgs<float> &a, const float *tot, const float *totU, const float *CA, const float *CB,
+                      const float *sq, float2 *out, int64_t Kp, int64_t nF) override {
+    return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
+  }
+  fst_status coef_mix(const CoefArgs<double> &a, const double *tot, const double *totU, const double *CA,
+                      const double *CB, const double *sq, double2 *out, int64_t Kp, int64_t nF) override {
+    return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
+  }
+
   fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
     for (int64_t i = 0; i < n; ++i) {
       hi[i] = tf32_round(src[i]);

@@ -644,8 +644,10 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
   return FST_OK;
 }
 
+static void free_coef(fst_plan_t p);
 void destroy_plan(fst_plan_t p) {
   if (!p) return;
+  if (p->R) free_coef(p);
   Runner *R = p->R;
   if (R) {
     R->sync();
@@ -746,5 +748,346 @@ fst_status fst_emu_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, doub
 }
 
 int fst_plan_is_emulated(fst_plan_t p) { return (p && p->R && !p->R->device()) ? 1 : 0; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Fast coefficient vector T2^* y (Theorem 1 construction, Section 2; Section 1.3)
+// ===========================================================================
+namespace fst {
+
+// Complete elliptic integral K and Jacobi dn for parameter m = 1 - m1, by the
+// arithmetic-geometric mean (Abramowitz & Stegun 17.6 and 16.4).
+static double agm_K(double m1) {
+  double a = 1.0, b = sqrt(m1);
+  for (int i = 0; i < 64 && fabs(a - b) > 1e-16 * a; ++i) {
+    const double an = 0.5 * (a + b);
+    b = sqrt(a * b);
+    a = an;
+  }
+  return M_PI / (2.0 * a);
+}
+static double jacobi_dn(double u, double m1) {
+  double a[80], c[80];
+  a[0] = 1.0;
+  double b = sqrt(m1);
+  c[0] = sqrt(1.0 - m1);
+  int n = 0;
+  while (n < 78 && fabs(c[n]) > 1e-17) {
+    a[n + 1] = 0.5 * (a[n] + b);
+    c[n + 1] = 0.5 * (a[n] - b);
+    b = sqrt(a[n] * b);
+    ++n;
+  }
+  double phi = ldexp(1.0, n) * a[n] * u;
+  double phi_next = phi;
+  for (int i = n; i >= 1; --i) {
+    phi_next = phi;
+    phi = 0.5 * (phi + asin(c[i] / a[i] * sin(phi)));
+  }
+  // phi = phi_0, phi_next = phi_1
+  return cos(phi) / cos(phi_next - phi);
+}
+
+// optimal CF-ADI shifts for A = diag(n + 1/2): p_k = b dn((2k-1)/(2r) K, m), m = 1 - (a/b)^2
+static std::vector<double> adi_shifts(int64_t N, int r) {
+  const double a = 0.5, b = (double)N - 0.5;
+  const double m1 = (a / b) * (a / b);
+  const double K = agm_K(m1);
+  std::vector<double> p(r);
+  for (int k = 1; k <= r; ++k) p[k - 1] = (N == 1) ? 0.5 : b * jacobi_dn((2.0 * k - 1.0) / (2.0 * r) * K, m1);
+  return p;
+}
+static double adi_error_bound(int64_t N, const std::vector<double> &p) {
+  double mx = 0.0;
+  for (int64_t n = 0; n < N; ++n) {
+    const double x = (double)n + 0.5;
+    double phi = 1.0;
+    for (double pj : p) phi *= (x - pj) / (x + pj);
+    mx = std::max(mx, phi * phi);
+  }
+  return mx;
+}
+
+static fst_status build_coef(fst_plan_t p) {
+  if (p->coef) return FST_OK;
+  Runner *R = p->R;
+  const int64_t N = p->N;
+  const double eps = p->eps, W = p->W;
+  CoefPlan *cp = new CoefPlan();
+  cp->odd = 2 * (int64_t)floor((double)N * W) + 1;
+  cp->h = (cp->odd - 1) / 2;
+  cp->Wp = (double)cp->odd / (2.0 * (double)N);
+  const double dH = 4.0 * M_PI * eps / 15.0, dA = 7.0 * eps / 30.0, dB = 7.0 * eps / 30.0;
+  int rH = (int)ceil(log(8.0 * (double)N - 4.0) * log(4.0 * M_PI / dH) / (M_PI * M_PI));
+  rH = std::max(rH, 1);
+  for (;;) {
+    cp->p = adi_shifts(N, rH);
+    if (adi_error_bound(N, cp->p) <= dH / M_PI || rH > 400) break;
+    ++rH;
+  }
+  cp->rH = rH;
+  cp->rA = std::max(1, (int)ceil(log(2.0 / (3.0 * M_PI * dA)) / (2.0 * log(2.0))));
+  cp->rB = std::max(1, (int)ceil(log(3.0 / (2.0 * dB)) / (2.0 * log(6.0 / M_PI))));
+  cp->DA = 2 * cp->rA;
+  cp->DB = 2 * cp->rB - 1;
+  cp->nraw = 4 * cp->rH + 2 * cp->DA + 2 * cp->DB;
+  cp->r1 = 4 * cp->rH + 2 * cp->DA + 2 * cp->DB;
+  // ADI recurrence factors
+  std::vector<double> zfirst(rH), zshift(rH);
+  for (int k = 0; k < rH; ++k) {
+    zshift[k] = cp->p[k];
+    zfirst[k] = (k == 0) ? sqrt(2.0 * cp->p[0]) : sqrt(cp->p[k] / cp->p[k - 1]);
+  }
+  // Taylor coefficients: alpha_k = 1 - (1 - 2^{1-2k}) zeta(2k) = sum_{n>=2} (-1)^n n^{-2k}
+  // (k = 1: 1 - pi^2/12), beta_k = (-1)^k t^{2k+1} / (2k+1)!, t = pi (W - W') N
+  std::vector<double> alpha(cp->rA + 1, 0.0), beta(cp->rB, 0.0);
+  for (int k = 1; k <= cp->rA; ++k) {
+    if (k == 1) { alpha[k] = 1.0 - M_PI * M_PI / 12.0; continue; }
+    double s = 0.0;
+    for (int n = 20000; n >= 2; --n) s += ((n & 1) ? -1.0 : 1.0) * pow((double)n, -2.0 * k);
+    alpha[k] = s;
+  }
+  const double t = M_PI * (W - cp->Wp) * (double)N;
+  {
+    double term = t;   // t^{2k+1} / (2k+1)! for k = 0
+    for (int k = 0; k < cp->rB; ++k) {
+      beta[k] = ((k & 1) ? -1.0 : 1.0) * term;
+      term *= t * t / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+  }
+  // C_A, C_B on centred monomials: (u_m - u_n)^d = sum_i C(d,i) u_m^i (-u_n)^{d-i}
+  const int Dmax = std::max(cp->DA, cp->DB) + 1;
+  std::vector<std::vector<double>> binom(Dmax, std::vector<double>(Dmax, 0.0));
+  for (int d = 0; d < Dmax; ++d) {
+    binom[d][0] = binom[d][d] = 1.0;
+    for (int i = 1; i < d; ++i) binom[d][i] = binom[d - 1][i - 1] + binom[d - 1][i];
+  }
+  const double sc = 2.0 / ((double)N * M_PI);
+  std::vector<double> CA((size_t)cp->DA * cp->DA, 0.0), CB((size_t)cp->DB * cp->DB, 0.0);
+  for (int k = 1; k <= cp->rA; ++k) {
+    const int d = 2 * k - 1;
+    for (int i = 0; i <= d; ++i) CA[(size_t)i * cp->DA + (d - i)] += sc * alpha[k] * binom[d][i] * (((d - i) & 1) ? -1.0 : 1.0);
+  }
+  for (int k = 0; k < cp->rB; ++k) {
+    const int d = 2 * k;
+    for (int i = 0; i <= d; ++i) CB[(size_t)i * cp->DB + (d - i)] += sc * beta[k] * binom[d][i] * (((d - i) & 1) ? -1.0 : 1.0);
+  }
+  std::vector<double> sqrtD(std::max<int64_t>(p->r, 1), 0.0);
+  for (int64_t j = 0; j < p->r; ++j) sqrtD[j] = sqrt(fabs(p->D[j]));
+  // phase ramps exp(-j 2 pi W' n) (exact reduction: W' n = odd n / 2N) and
+  // exp(-j pi (W + W') n) (product split exactly with fma before reducing mod 2)
+  std::vector<double2> phA(N), phB(N);
+  const double sW = W + cp->Wp;
+  for (int64_t n = 0; n < N; ++n) {
+    const int64_t m = (int64_t)(((__int128)cp->odd * n) % (2 * N));   // W' n = m / (2N) cycles
+    const double ang = M_PI * ((double)m / (double)N);
+    phA[n] = make_double2(cos(ang), -sin(ang));
+    const double hi = sW * (double)n, lo = fma(sW, (double)n, -hi);
+    double r = fmod(hi, 2.0) + lo;
+    phB[n] = make_double2(cos(M_PI * r), -sin(M_PI * r));
+  }
+  auto up64 = [&](double **dst, const std::vector<double> &v) -> fst_status {
+    TRY(R->alloc((void **)dst, v.size() * sizeof(double)));
+    return R->h2d(*dst, v.data(), v.size() * sizeof(double));
+  };
+  auto up32 = [&](float **dst, const std::vector<double> &v) -> fst_status {
+    std::vector<float> f(v.begin(), v.end());
+    TRY(R->alloc((void **)dst, f.size() * sizeof(float)));
+    return R->h2d(*dst, f.data(), f.size() * sizeof(float));
+  };
+  fst_status st = FST_OK;
+  if ((st = up64(&cp->zfirst64, zfirst)) || (st = up64(&cp->zshift64, zshift)) || (st = up64(&cp->CA64, CA)) ||
+      (st = up64(&cp->CB64, CB)) || (st = up64(&cp->sqrtD64, sqrtD)) || (st = up32(&cp->zfirst32, zfirst)) ||
+      (st = up32(&cp->zshift32, zshift)) || (st = up32(&cp->CA32, CA)) || (st = up32(&cp->CB32, CB)) ||
+      (st = up32(&cp->sqrtD32, sqrtD))) {
+    p->coef = cp;
+    return st;
+  }
+  {
+    std::vector<float2> a32(N), b32(N);
+    for (int64_t n = 0; n < N; ++n) {
+      a32[n] = make_float2((float)phA[n].x, (float)phA[n].y);
+      b32[n] = make_float2((float)phB[n].x, (float)phB[n].y);
+    }
+    p->coef = cp;
+    TRY(R->alloc((void **)&cp->phA64, N * sizeof(double2)));
+    TRY(R->alloc((void **)&cp->phB64, N * sizeof(double2)));
+    TRY(R->alloc((void **)&cp->phA32, N * sizeof(float2)));
+    TRY(R->alloc((void **)&cp->phB32, N * sizeof(float2)));
+    TRY(R->h2d(cp->phA64, phA.data(), N * sizeof(double2)));
+    TRY(R->h2d(cp->phB64, phB.data(), N * sizeof(double2)));
+    TRY(R->h2d(cp->phA32, a32.data(), N * sizeof(float2)));
+    TRY(R->h2d(cp->phB32, b32.data(), N * sizeof(float2)));
+  }
+  return FST_OK;
+}
+
+static void free_coef(fst_plan_t p) {
+  CoefPlan *cp = p->coef;
+  if (!cp) return;
+  void *bufs[] = {cp->zfirst32, cp->zshift32, cp->CA32, cp->CB32, cp->sqrtD32, cp->zfirst64, cp->zshift64,
+                  cp->CA64, cp->CB64, cp->sqrtD64, cp->phA32, cp->phB32, cp->phA64, cp->phB64};
+  for (void *b : bufs)
+    if (b) p->R->release(b);
+  delete cp;
+  p->coef = nullptr;
+}
+
+template <typename T> struct CoefPtrs;
+template <> struct CoefPtrs<float> {
+  static void fill(const CoefPlan *c, CoefArgs<float> &a, const float *&CA, const float *&CB, const float *&sq) {
+    a.zfirst = c->zfirst32; a.zshift = c->zshift32; a.phA = c->phA32; a.phB = c->phB32;
+    CA = c->CA32; CB = c->CB32; sq = c->sqrtD32;
+  }
+};
+template <> struct CoefPtrs<double> {
+  static void fill(const CoefPlan *c, CoefArgs<double> &a, const double *&CA, const double *&CB, const double *&sq) {
+    a.zfirst = c->zfirst64; a.zshift = c->zshift64; a.phA = c->phA64; a.phB = c->phB64;
+    CA = c->CA64; CB = c->CB64; sq = c->sqrtD64;
+  }
+};
+
+template <typename T>
+static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, int64_t ld, bool cplx) {
+  using C = c2<T>;
+  Runner *R = p->R;
+  TRY(build_coef(p));
+  const CoefPlan *cp = p->coef;
+  const int64_t N = p->N;
+  const int64_t nF = cp->odd;
+  const int64_t Kp = nF + cp->r1 + p->r;
+  const bool dbl = sizeof(T) == 8;
+  int log2N = 0;
+  while ((1LL << log2N) < N) ++log2N;
+  // ---- F^* y: forward DFT of length N, chunk by chunk of pairs, then the bins
+  Layout Lf = make_layout(N, log2N, dbl, 0, false);
+  if (!Lf.small) Lf.Pnz = 1 << Lf.log2P;
+  const int64_t npairs = cplx ? batch : (batch + 1) / 2;
+  const size_t ws_f = (size_t)Lf.chunk * N * sizeof(C) + (size_t)Lf.chunk * std::max(Lf.ntiles, 1) * 2 * sizeof(T) * 8 + 4096;
+  const int nchunks = (int)((N + COEF_CHUNK - 1) / COEF_CHUNK);
+  const size_t part_b = (size_t)batch * nchunks * cp->nraw * 2 * sizeof(T);
+  const size_t partU_b = (size_t)batch * nchunks * std::max<int64_t>(p->r, 1) * 2 * sizeof(T);
+  const size_t tot_b = (size_t)batch * cp->nraw * 2 * sizeof(T);
+  const size_t totU_b = (size_t)batch * std::max<int64_t>(p->r, 1) * 2 * sizeof(T);
+  TRY(ensure_ws(p, std::max(ws_f, part_b + partU_b + tot_b + totU_b + 4096)));
+  {
+    ConvArgs<T> a{};
+    a.y = y;
+    a.ld = ld;
+    a.batch = batch;
+    a.cplx = cplx ? 1 : 0;
+    a.N = N;
+    a.r = 0;
+    a.rpad = 0;
+    a.tw = plan_tw<T>(p);
+    a.mode = MODE_FORWARD;
+    a.log2M = Lf.log2M;
+    a.log2P = Lf.log2P;
+    a.log2Q = Lf.log2Q;
+    a.Pnz = Lf.Pnz;
+    a.NB = Lf.NB;
+    a.G = Lf.G;
+    char *w = (char *)p->ws;
+    a.inter = (C *)w;
+    if (!Lf.small) {
+      a.part = (T *)(w + (size_t)Lf.chunk * N * sizeof(C));
+      a.acoef = a.part;
+    }
+    for (int64_t p0 = 0; p0 < npairs; p0 += Lf.chunk) {
+      a.pair0 = p0;
+      a.npairs = std::min<int64_t>(Lf.chunk, npairs - p0);
+      if (Lf.small) {
+        TRY(R->small(a, Lf));
+      } else {
+        TRY(R->passA(a, Lf));
+        TRY(R->passB(a, Lf));
+      }
+      const int64_t sig0 = cplx ? p0 : 2 * p0;
+      const int64_t nsig = cplx ? a.npairs : std::min<int64_t>(2 * a.npairs, batch - sig0);
+      TRY(R->coef_gather(a.inter, Lf, N, a.cplx, sig0, nsig, cp->h, out, Kp));
+    }
+  }
+  // ---- L2^* y and U2^* y
+  CoefArgs<T> c{};
+  c.y = y;
+  c.ld = ld;
+  c.batch = batch;
+  c.cplx = cplx ? 1 : 0;
+  c.N = N;
+  c.rH = cp->rH;
+  c.DA = cp->DA;
+  c.DB = cp->DB;
+  c.nraw = cp->nraw;
+  c.nchunks = nchunks;
+  char *w = (char *)p->ws;
+  c.part = (T *)w;
+  c.partU = (T *)(w + part_b);
+  T *tot = (T *)(w + part_b + partU_b);
+  T *totU = (T *)(w + part_b + partU_b + tot_b);
+  c.ST = (const T *)(dbl ? (const void *)p->ST64 : (const void *)p->ST32);
+  c.r = (int)p->r;
+  c.rpad = (int)p->rpad;
+  const T *CA, *CB, *sq;
+  CoefPtrs<T>::fill(cp, c, CA, CB, sq);
+  TRY(R->coef_lowrank(c));
+  if (p->r > 0) TRY(R->coef_st(c));
+  TRY(R->coef_reduce(c.part, nchunks, cp->nraw, batch, tot));
+  if (p->r > 0) TRY(R->coef_reduce(c.partU, nchunks, (int)p->r, batch, totU));
+  TRY(R->coef_mix(c, tot, totU, CA, CB, sq, out, Kp, nF));
+  return FST_OK;
+}
+
+static fst_status run_coeffs(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FST_EINVAL, "batch < 0");
+  if (batch == 0) return FST_OK;
+  if (!y || !out) return fail(FST_EINVAL, "NULL pointer");
+  if (ld == 0) ld = p->N;
+  if (ld < p->N) return fail(FST_EINVAL, "ld < N");
+  if (p->op != FST_OP_PROJECT) return fail(FST_EINVAL, "coefficients need a projection plan");
+  if ((p->N & (p->N - 1)) != 0) return fail(FST_EUNSUPPORTED, "coefficients need N a power of two");
+  switch (dtype) {
+    case FST_F32: return coeffs_t<float>(p, (const float *)y, (float2 *)out, batch, ld, false);
+    case FST_C64: return coeffs_t<float>(p, (const float *)y, (float2 *)out, batch, ld, true);
+    case FST_F64: return coeffs_t<double>(p, (const double *)y, (double2 *)out, batch, ld, false);
+    case FST_C128: return coeffs_t<double>(p, (const double *)y, (double2 *)out, batch, ld, true);
+    default: return fail(FST_EINVAL, "unknown dtype");
+  }
+}
+
+}  // namespace fst
+
+extern "C" {
+
+fst_status fst_coeffs(fst_plan_t p, const void *y, void *coeffs, int64_t batch, int64_t ld, int dtype,
+                      void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  p->R->set_stream(stream);
+  return run_coeffs(p, y, coeffs, batch, ld, dtype);
+}
+
+fst_status fst_coeffs_info(fst_plan_t p, int64_t *Kprime, int64_t *nF, int64_t *r1, int64_t *rH, int64_t *rA,
+                           int64_t *rB) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if ((p->N & (p->N - 1)) != 0) return fail(FST_EUNSUPPORTED, "coefficients need N a power of two");
+  fst_status s = build_coef(p);
+  if (s != FST_OK) return s;
+  const CoefPlan *cp = p->coef;
+  if (Kprime) *Kprime = cp->odd + cp->r1 + p->r;
+  if (nF) *nF = cp->odd;
+  if (r1) *r1 = cp->r1;
+  if (rH) *rH = cp->rH;
+  if (rA) *rA = cp->rA;
+  if (rB) *rB = cp->rB;
+  return FST_OK;
+}
+
+fst_status fst_adi_shifts(int64_t N, int r, double *out) {
+  if (N < 1 || r < 1 || !out) return fail(FST_EINVAL, "bad arguments");
+  std::vector<double> p = fst::adi_shifts(N, r);
+  memcpy(out, p.data(), r * sizeof(double));
+  return FST_OK;
+}
 
 }  // extern "C"

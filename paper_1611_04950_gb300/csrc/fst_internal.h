@@ -15,29 +15,11 @@
 #include "../../include/fst.h"
 #include "fst_kernels.cuh"
 #include "fst_plan_kernels.cuh"
+#include "fst_coeffs.cuh"
 
 namespace fst {
 
-// Launch layout of the length-M transform for one real type.
-struct Layout {
-  bool small = true;
-  bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
-  bool fused_reduce = false;  // the row pass also sums the correction partials (device fast path, Q = 4096)
-  int log2M = 0, log2P = 0, log2Q = 0;
-  int Pnz = 0, NB = 0, G = 1, ntiles = 0;
-  int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
-  size_t smem_small = 0, smem_A = 0, smem_B = 0, smem_C = 0;
-  int64_t chunk = 1;   // pairs per launch group
-};
-
 Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast = false);
-// position of natural frequency index k in the layout's spectrum array
-__host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
-  if (L.small) return k;
-  const int64_t P = 1LL << L.log2P;
-  return (k & (P - 1)) * (1LL << L.log2Q) + (k >> L.log2P);
-}
-
 struct Runner {
   virtual ~Runner() {}
   virtual bool device() const = 0;
@@ -87,6 +69,22 @@ struct Runner {
                                float *ST32) = 0;
   virtual fst_status to_f32(const double *src, float *dst, int64_t n) = 0;
   virtual fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) = 0;
+
+  // fast coefficient vector kernels (runner memory)
+  virtual fst_status coef_lowrank(const CoefArgs<float> &a) = 0;
+  virtual fst_status coef_lowrank(const CoefArgs<double> &a) = 0;
+  virtual fst_status coef_st(const CoefArgs<float> &a) = 0;
+  virtual fst_status coef_st(const CoefArgs<double> &a) = 0;
+  virtual fst_status coef_reduce(const float *part, int nchunks, int nout, int64_t batch, float *tot) = 0;
+  virtual fst_status coef_reduce(const double *part, int nchunks, int nout, int64_t batch, double *tot) = 0;
+  virtual fst_status coef_gather(const float2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0,
+                                 int64_t nsig, int64_t h, float2 *out, int64_t Kp) = 0;
+  virtual fst_status coef_gather(const double2 *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0,
+                                 int64_t nsig, int64_t h, double2 *out, int64_t Kp) = 0;
+  virtual fst_status coef_mix(const CoefArgs<float> &a, const float *tot, const float *totU, const float *CA,
+                              const float *CB, const float *sqrtD, float2 *out, int64_t Kp, int64_t nF) = 0;
+  virtual fst_status coef_mix(const CoefArgs<double> &a, const double *tot, const double *totU, const double *CA,
+                              const double *CB, const double *sqrtD, double2 *out, int64_t Kp, int64_t nF) = 0;
 };
 
 Runner *make_dev_runner();
@@ -94,8 +92,23 @@ Runner *make_emu_runner();
 
 }  // namespace fst
 
+namespace fst {
+// Lazily built data of the fast coefficient vector T2^* y (Theorem 1 construction).
+struct CoefPlan {
+  int64_t odd = 0, h = 0;        // 2NW' = odd = 2h + 1
+  double Wp = 0;
+  int rH = 0, rA = 0, rB = 0, DA = 0, DB = 0, nraw = 0, r1 = 0;
+  std::vector<double> p;         // ADI shifts
+  float *zfirst32 = nullptr, *zshift32 = nullptr, *CA32 = nullptr, *CB32 = nullptr, *sqrtD32 = nullptr;
+  double *zfirst64 = nullptr, *zshift64 = nullptr, *CA64 = nullptr, *CB64 = nullptr, *sqrtD64 = nullptr;
+  float2 *phA32 = nullptr, *phB32 = nullptr;
+  double2 *phA64 = nullptr, *phB64 = nullptr;
+};
+}  // namespace fst
+
 struct fst_plan_s {
   fst::Runner *R = nullptr;
+  fst::CoefPlan *coef = nullptr;
   int64_t N = 0, K = 0, M = 0, r = 0, rpad = 0, win_lo = 0, win_hi = 0;
   int log2M = 0;
   double W = 0, eps = 0, alpha = 0, beta = 1;

@@ -34,6 +34,27 @@ namespace fst {
 
 enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2 };
 
+// Launch layout of the length-M transform for one real type.
+struct Layout {
+  bool small = true;
+  bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
+  bool fused_reduce = false;  // the row pass also sums the correction partials (device fast path, Q = 4096)
+  int log2M = 0, log2P = 0, log2Q = 0;
+  int Pnz = 0, NB = 0, G = 1, ntiles = 0;
+  int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
+  size_t smem_small = 0, smem_A = 0, smem_B = 0, smem_C = 0;
+  int64_t chunk = 1;   // pairs per launch group
+};
+
+// position of natural frequency index k in the layout's spectrum array
+__host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
+  if (L.small) return k;
+  const int64_t P = 1LL << L.log2P;
+  return (k & (P - 1)) * (1LL << L.log2Q) + (k >> L.log2P);
+}
+
+
+
 template <typename T> struct ConvArgs {
   // signals
   const T *y;         // real: batch rows of N (stride ld); complex: batch rows of N pairs (stride ld pairs)

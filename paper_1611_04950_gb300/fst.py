@@ -33,7 +33,8 @@ EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_
             "fst_project_host", "fst_apply_prolate", "fst_destroy", "fst_last_error", "fst_version",
             "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
             "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
-            "fst_project_noalloc", "fst_noalloc_scratch_bytes"]
+            "fst_project_noalloc", "fst_noalloc_scratch_bytes", "fst_coeffs", "fst_coeffs_info",
+            "fst_adi_shifts"]
 
 
 class FSTError(RuntimeError):
@@ -63,6 +64,9 @@ def _load():
         "fst_plan_is_emulated": ([P], I),
         "fst_launch_count": ([], C.c_longlong),
         "fst_project_noalloc": ([P, vp, vp, i64, i64, I, vp], I),
+        "fst_coeffs": ([P, vp, vp, i64, i64, I, vp], I),
+        "fst_coeffs_info": ([P] + [C.POINTER(i64)] * 6, I),
+        "fst_adi_shifts": ([i64, I, C.POINTER(d)], I),
         "fst_noalloc_scratch_bytes": ([], C.c_ulonglong),
         "fst_profile_enable": ([I], I),
         "fst_profile_count": ([], I),
@@ -155,6 +159,23 @@ def fst_project_noalloc(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, d
 
 def fst_noalloc_scratch_bytes() -> int:
     return int(_lib.fst_noalloc_scratch_bytes())
+
+
+def fst_coeffs(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dtype: int, stream: int = 0):
+    _check(_lib.fst_coeffs(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, ld, dtype,
+                           C.c_void_p(stream)))
+
+
+def fst_coeffs_info(h: int) -> dict:
+    v = [C.c_int64() for _ in range(6)]
+    _check(_lib.fst_coeffs_info(C.c_void_p(h), *[C.byref(x) for x in v]))
+    return dict(zip(["Kprime", "nF", "r1", "rH", "rA", "rB"], [x.value for x in v]))
+
+
+def fst_adi_shifts(N: int, r: int) -> np.ndarray:
+    out = np.zeros(r)
+    _check(_lib.fst_adi_shifts(N, r, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
 
 
 def fst_destroy(h: int):
@@ -265,6 +286,27 @@ class Plan:
     def apply_prolate(self, y, out=None, stream=None):
         """B_{N,W} y alone."""
         return self._run(fst_apply_prolate, y, out, stream)
+
+    def coeffs(self, y, stream=None):
+        """Fast coefficient vector T2^* y, (batch, K') complex (Section 1.3, fast factorization)."""
+        info = fst_coeffs_info(self.h)
+        Kp = info["Kprime"]
+        if self.emulated:
+            y = np.ascontiguousarray(np.asarray(y))
+            if y.ndim == 1:
+                y = y[None]
+            ct = np.complex128 if y.dtype in (np.float64, np.complex128) else np.complex64
+            out = np.zeros((y.shape[0], Kp), ct)
+            fst_coeffs(self.h, y.ctypes.data, out.ctypes.data, y.shape[0], y.shape[1], _dtype_code(y.dtype), 0)
+            return out
+        import torch
+        if y.dim() == 1:
+            y = y.unsqueeze(0)
+        ct = torch.complex128 if y.dtype in (torch.float64, torch.complex128) else torch.complex64
+        out = torch.zeros((y.shape[0], Kp), dtype=ct, device=y.device)
+        ld = y.stride(0) if y.shape[0] > 1 else self.N
+        fst_coeffs(self.h, y.data_ptr(), out.data_ptr(), y.shape[0], ld, _dtype_code(y.dtype), _stream_handle(stream))
+        return out
 
     def project_host(self, y, out=None, stream=None):
         """P_fast y for a (batch, N) HOST array / tensor (copies inside the call)."""

@@ -186,3 +186,57 @@ def test_repeatability_bit_for_bit():
     a = p.project(y)
     b = p.project(y)
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- fast coefficient vector
+
+def test_adi_shifts_match_scipy():
+    from oracle import thm1 as T
+    for N, r in [(1, 2), (64, 7), (4096, 18), (65536, 16), (1 << 22, 38)]:
+        got = F.fst_adi_shifts(N, r)
+        ref = T.adi_shifts(N, r)
+        assert np.max(np.abs(got - ref) / ref) < 1e-6
+
+
+@pytest.mark.parametrize("N,W,eps", [(256, 1 / 16, 1e-6), (1024, 0.2, 1e-4), (4096, 1 / 16, 1e-6),
+                                     (32768, 0.25, 1e-8), (2, 0.3, 1e-3)])
+def test_emulated_coeffs_match_oracle(N, W, eps):
+    from oracle import thm1 as T
+    p = P.Plan(N, W, eps=eps, emulate=True)
+    t = T.thm1(N, W, eps)
+    op = O.make_plan(N, W, None, eps)
+    info = F.fst_coeffs_info(p.h)
+    assert (info["rH"], info["rA"], info["rB"], info["r1"]) == (t.r_H, t.r_A, t.r_B, t.r1)
+    assert info["Kprime"] == t.nF + t.r1 + op.r
+    rng = np.random.default_rng(N)
+    y = rng.standard_normal((3, N))
+    ref = T.coeffs(t, op, y.T).T
+    nrm = np.linalg.norm(y, axis=1)[:, None]
+    assert np.all(np.abs(p.coeffs(y) - ref) <= 1e-12 * nrm)
+    assert np.all(np.abs(p.coeffs(y.astype(np.float32)) - ref) <= 1e-6 * nrm)
+    yc = rng.standard_normal((2, N)) + 1j * rng.standard_normal((2, N))
+    refc = T.coeffs(t, op, yc.T).T
+    assert np.all(np.abs(p.coeffs(yc) - refc) <= 1e-12 * np.linalg.norm(yc, axis=1)[:, None])
+
+
+def test_emulated_coeffs_expand_to_projection():
+    from oracle import thm1 as T
+    N, W, eps = 512, 0.2, 1e-6
+    p = P.Plan(N, W, eps=eps, emulate=True)
+    t = T.thm1(N, W, eps)
+    op = O.make_plan(N, W, None, eps)
+    y = np.random.default_rng(3).standard_normal(N)
+    c = p.coeffs(y)[0]
+    back = T.expand(t, op, c)
+    assert np.linalg.norm(back - O.exact_project(N, W, p.K, y)) <= 2 * eps * np.linalg.norm(y)
+
+
+def test_coeffs_need_power_of_two_and_projection():
+    p = P.Plan(100, 0.1, eps=1e-6, emulate=True)
+    with pytest.raises(F.FSTError) as ei:
+        p.coeffs(np.zeros((1, 100)))
+    assert ei.value.status == F.FST_EUNSUPPORTED
+    q = P.Plan(128, 0.1, eps=1e-6, op="pinv", emulate=True)
+    with pytest.raises(F.FSTError) as ei:
+        q.coeffs(np.zeros((1, 128)))
+    assert ei.value.status == F.FST_EINVAL

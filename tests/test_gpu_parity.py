@@ -208,3 +208,80 @@ def test_repeatable_bit_for_bit():
     b = p.project(y)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+# ---------------------------------------------------------------- fast coefficient vector
+
+@pytest.mark.parametrize("N,W,eps", [(4096, 1 / 16, 1e-6), (65536, 0.25, 1e-8)])
+def test_coeffs_against_oracle(N, W, eps):
+    from oracle import thm1 as T
+    dev = _cuda()
+    p = F.Plan(N, W, eps=eps)
+    t = T.thm1(N, W, eps)
+    o = oplan(N, W, p.K, eps)
+    y = workloads.gaussian(3, N, seed=21)
+    ref = T.coeffs(t, o, y.numpy().T).T
+    nrm = np.linalg.norm(y.numpy(), axis=1)[:, None]
+    c64 = p.coeffs(y.to(dev)).cpu().numpy()
+    c32 = p.coeffs(y.float().to(dev)).cpu().numpy()
+    assert c64.shape == ref.shape
+    assert np.all(np.abs(c64 - ref) <= 1e-11 * nrm)
+    assert np.all(np.abs(c32 - ref) <= 1e-5 * nrm)
+    if N <= 8192:
+        back = T.expand(t, o, c32[0].astype(np.complex128))
+        ex = O.exact_project(N, W, p.K, y.numpy()[0])
+        assert np.linalg.norm(back - ex) <= (2 * eps + 1e-5) * nrm[0, 0]
+
+
+def test_coeffs_complex_input():
+    from oracle import thm1 as T
+    dev = _cuda()
+    N, W, eps = 8192, 0.05, 1e-6
+    p = F.Plan(N, W, eps=eps)
+    t = T.thm1(N, W, eps)
+    o = oplan(N, W, p.K, eps)
+    y = workloads.gaussian(2, N, seed=5, complex_=True)
+    ref = T.coeffs(t, o, y.numpy().T).T
+    got = p.coeffs(y.to(torch.complex64).to(dev)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.linalg.norm(y.numpy(), axis=1)[:, None])
+
+
+# ---------------------------------------------------------------- full-size workloads, sampled
+
+def test_c1m_complex_full_batch_sampled():
+    # N = 2^20, W = 0.05, eps = 1e-6, 64 complex64 signals (half band-limited), one call
+    _cuda()
+    wl = workloads.c1m(batch=64, device="cuda")
+    p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    out = p.project(wl.y)
+    torch.cuda.synchronize()
+    o = oplan(wl.N, wl.W, p.K, wl.eps)
+    assert p.r == o.r
+    idx = [0, 63]
+    y = wl.y[idx].to(torch.complex128).cpu().numpy()
+    fast = O.fast_project(o, y.T).T
+    e = rel_err(out[idx].cpu().numpy(), fast, y)
+    assert np.all(e < 1e-5), e
+
+
+def test_c4m_full_batch_sampled_projection_and_coeffs():
+    # N = 2^22, W = 1/4, eps = 1e-8, 16 real FP32 signals: projection and coefficient vector
+    from oracle import thm1 as T
+    _cuda()
+    wl = workloads.c4m(batch=16, device="cuda")
+    p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    out = p.project(wl.y)
+    coef = p.coeffs(wl.y)
+    torch.cuda.synchronize()
+    o = oplan(wl.N, wl.W, p.K, wl.eps)
+    assert p.r == o.r
+    idx = [0, 15]
+    y = wl.y[idx].double().cpu().numpy()
+    fast = O.fast_project(o, y.T).T
+    e = rel_err(out[idx].cpu().numpy(), fast, y)
+    assert np.all(e < 1e-5), e
+    t = T.thm1(wl.N, wl.W, wl.eps)
+    ref = T.coeffs(t, o, y.T).T
+    c = coef[idx].cpu().numpy()
+    assert c.shape == ref.shape
+    assert np.all(np.abs(c - ref) <= 1e-5 * np.linalg.norm(y, axis=1)[:, None])
