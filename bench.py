@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--coeffs", default="auto", choices=["auto", "on", "off"],
+                    help="also compute the fast coefficient vector each step (auto: on for c4m)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -215,9 +217,21 @@ def main():
     B, N = y.shape
     plan = F.Plan(N, wl.W, eps=wl.eps)
     stream = torch.cuda.current_stream()
+    with_coeffs = args.coeffs == "on" or (args.coeffs == "auto" and args.workload == "c4m")
+    coef_buf = None
+    if with_coeffs:
+        Kp = F.fst_coeffs_info(plan.h)["Kprime"]
+        ct = torch.complex128 if y.dtype in (torch.float64, torch.complex128) else torch.complex64
+        coef_buf = torch.empty((B, Kp), dtype=ct, device=y.device)
+
+    def step():
+        plan.project(y, out)
+        if with_coeffs:
+            F.fst_coeffs(plan.h, y.data_ptr(), coef_buf.data_ptr(), B, N, F._dtype_code(y.dtype),
+                         stream.cuda_stream)
 
     for _ in range(args.warmup):
-        plan.project(y, out)
+        step()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -228,7 +242,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.project(y, out)
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -245,7 +259,7 @@ def main():
     # per-kernel launch times (separate pass with events around every launch)
     F.fst_profile_enable(True)
     for _ in range(3):
-        plan.project(y, out)
+        step()
     torch.cuda.synchronize()
     recs = F.fst_profile_records()
     F.fst_profile_enable(False)
@@ -314,6 +328,7 @@ def main():
             "dtype": "c64" if y.is_complex() else "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "N": N, "W": wl.W, "eps": wl.eps,
                        "batch_per_gpu": B, "K": plan.K, "r": plan.r, "M": plan.M,
+                       "step": "projection + fast coefficient vector" if with_coeffs else "projection",
                        "l2": f"inputs {B * sig_bytes / 2**20:.0f} MiB + outputs of the same size exceed "
                              f"the 129 MB L2; no flush"},
             "gpu_launches": launches,

@@ -49,6 +49,16 @@ template <typename T> struct CState {
   T acc[2 * COEF_GROUP];
 };
 
+// a / b: the device's fast FP32 division (2 ulp) for the ADI recurrence; exact otherwise
+FST_HD float coef_div(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+FST_HD double coef_div(double a, double b) { return a / b; }
+
 template <typename T> FST_HD c2<T> coef_sample(const CoefArgs<T> &a, int64_t sig, int64_t n) {
   if (a.cplx) return reinterpret_cast<const c2<T> *>(a.y)[sig * a.ld + n];
   return mk<T>(a.y[sig * a.ld + n], (T)0);
@@ -93,9 +103,12 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
   const int64_t n0 = (int64_t)chunk * COEF_CHUNK;
   T *out = a.part + ((sig * a.nchunks + chunk) * a.nraw) * 2;
   const T half = (T)0.5, Nd = (T)a.N, cen = (T)(0.5 * (double)(a.N - 1)), invN = (T)(1.0 / (double)a.N);
-  int obase = 0;
+  const int vbase[4] = {0, 2 * a.rH + a.DA, 4 * a.rH + 2 * a.DA, 4 * a.rH + 2 * a.DA + a.DB};
   for (int variant = 0; variant < 4; ++variant) {
     const bool useA = variant < 2, conjph = (variant & 1) != 0;
+    // real input: the D_A y and D_B y sums are the conjugates of the D_A^* y, D_B^* y ones
+    if (!a.cplx && conjph) continue;
+    int obase = vbase[variant];
     // v(n) = phase(n) y(n) with phase = exp(-j..) (conjph: exp(+j..)); reset recurrences
     ex.phase([&](int tid, St &st) {
       for (int e = 0; e < COEF_E; ++e) {
@@ -107,8 +120,8 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
           if (conjph) ph = cconj(ph);
           v = cmul(ph, coef_sample(a, sig, n));
           const T x = (T)n + half, xr = Nd - x;      // x for n and for N-1-n
-          zf = a.zfirst[0] / (x + a.zshift[0]);
-          zr = a.zfirst[0] / (xr + a.zshift[0]);
+          zf = coef_div(a.zfirst[0], x + a.zshift[0]);
+          zr = coef_div(a.zfirst[0], xr + a.zshift[0]);
         }
         st.v[e] = v;
         st.zf[e] = zf;
@@ -129,8 +142,8 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
               if (k > 0 && n < a.N) {
                 const T x = (T)n + half, xr = Nd - x;
                 const T pk = a.zshift[k], pk1 = a.zshift[k - 1], sc = a.zfirst[k];
-                st.zf[e] = sc * (x - pk1) / (x + pk) * st.zf[e];
-                st.zr[e] = sc * (xr - pk1) / (xr + pk) * st.zr[e];
+                st.zf[e] = coef_div(sc * (x - pk1) * st.zf[e], x + pk);
+                st.zr[e] = coef_div(sc * (xr - pk1) * st.zr[e], xr + pk);
               }
               st.acc[4 * kk + 0] += st.zf[e] * st.v[e].x;
               st.acc[4 * kk + 1] += st.zf[e] * st.v[e].y;
@@ -155,6 +168,7 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
       }
       obase += 2 * a.rH;
     }
+    (void)obase;
     // monomials u^i, i < D
     const int D = useA ? a.DA : a.DB;
     for (int i0 = 0; i0 < D; i0 += COEF_GROUP) {
@@ -180,7 +194,17 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
         }
       });
     }
-    obase += D;
+  }
+  if (!a.cplx) {
+    ex.phase([&](int tid, St &) {
+      const int n0c = 2 * a.rH + a.DA, n2c = a.DB;
+      for (int i = tid; i < n0c + n2c; i += nthr) {
+        const int src = (i < n0c) ? vbase[0] + i : vbase[2] + (i - n0c);
+        const int dst = (i < n0c) ? vbase[1] + i : vbase[3] + (i - n0c);
+        out[2 * dst] = out[2 * src];
+        out[2 * dst + 1] = -out[2 * src + 1];
+      }
+    });
   }
 }
 

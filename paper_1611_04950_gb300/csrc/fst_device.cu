@@ -438,6 +438,26 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
+  fst_status corr_c(const ConvArgs<float> &a) override {
+    FastArgs f{a, a.ST_hi, a.ST_lo};
+    dim3 grid((unsigned)((a.N + CORR_ROWS - 1) / CORR_ROWS), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
+    PROF("k_corr_c", a.npairs, (k_corr_c<<<grid, FAST_THREADS, 0, cur>>>(f)));
+    LAUNCHED("k_corr_c");
+    return FST_OK;
+  }
+  fst_status corr_reduce(const ConvArgs<float> &a) override {
+    const int thr = std::min(1024, std::max(32, ((2 * a.r + 31) / 32) * 32));
+    PROF("k_corr_reduce", a.npairs, (k_corr_reduce<<<(unsigned)a.npairs, thr, 0, cur>>>(a)));
+    LAUNCHED("k_corr_reduce");
+    return FST_OK;
+  }
+  fst_status corr_z(const ConvArgs<float> &a) override {
+    FastArgs f{a, a.ST_hi, a.ST_lo};
+    dim3 grid((unsigned)((a.N + CORR_ROWS - 1) / CORR_ROWS), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
+    PROF("k_corr_z", a.npairs, (k_corr_z<<<grid, FAST_THREADS, 0, cur>>>(f)));
+    LAUNCHED("k_corr_z");
+    return FST_OK;
+  }
   fst_status passC(const ConvArgs<float> &a, const Layout &L) override {
     if (!L.fast) return passC_t(a, L);
     FastArgs f{a, a.ST_hi, a.ST_lo};
@@ -493,32 +513,28 @@ struct DevRunner : Runner {
   template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
     const size_t smem = (2 * COEF_GROUP * COEF_THREADS + 16 * 8 + 16) * sizeof(T);
     dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
-    k_coef_lowrank<T><<<grid, COEF_THREADS, smem, s>>>(a);
+    PROF("k_coef_lowrank", 0, (k_coef_lowrank<T><<<grid, COEF_THREADS, smem, cur>>>(a)));
     LAUNCHED("k_coef_lowrank");
-    ++g_launches;
     return FST_OK;
   }
   template <typename T> fst_status coef_st_t(const CoefArgs<T> &a) {
     const size_t smem = (COEF_THREADS / 32) * 128 * sizeof(T);
     dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
-    k_coef_st<T><<<grid, COEF_THREADS, smem, s>>>(a);
+    PROF("k_coef_st", 0, (k_coef_st<T><<<grid, COEF_THREADS, smem, cur>>>(a)));
     LAUNCHED("k_coef_st");
-    ++g_launches;
     return FST_OK;
   }
   template <typename T> fst_status coef_reduce_t(const T *part, int nchunks, int nout, int64_t batch, T *tot) {
     dim3 grid((unsigned)((nout + 127) / 128), (unsigned)batch);
-    k_coef_reduce<T><<<grid, 128, 0, s>>>(part, nchunks, nout, tot);
+    PROF("k_coef_reduce", 0, (k_coef_reduce<T><<<grid, 128, 0, cur>>>(part, nchunks, nout, tot)));
     LAUNCHED("k_coef_reduce");
-    ++g_launches;
     return FST_OK;
   }
   template <typename T>
   fst_status coef_gather_t(const c2<T> *X, const Layout &Lf, int64_t N, int cplx, int64_t sig0, int64_t nsig,
                            int64_t h, c2<T> *out, int64_t Kp) {
-    k_coef_gather<T><<<grid_for(nsig * (2 * h + 1), 256), 256, 0, s>>>(X, Lf, N, cplx, sig0, nsig, h, out, Kp);
+    PROF("k_coef_gather", 0, (k_coef_gather<T><<<grid_for(nsig * (2 * h + 1), 256), 256, 0, cur>>>(X, Lf, N, cplx, sig0, nsig, h, out, Kp)));
     LAUNCHED("k_coef_gather");
-    ++g_launches;
     return FST_OK;
   }
   template <typename T>
@@ -526,9 +542,8 @@ struct DevRunner : Runner {
                         c2<T> *out, int64_t Kp, int64_t nF) {
     const int nfin = 4 * a.rH + 2 * a.DA + 2 * a.DB + a.r;
     dim3 grid((unsigned)((nfin + 127) / 128), (unsigned)a.batch);
-    k_coef_mix<T><<<grid, 128, 0, s>>>(a, tot, totU, CA, CB, sq, out, Kp, nF);
+    PROF("k_coef_mix", 0, (k_coef_mix<T><<<grid, 128, 0, cur>>>(a, tot, totU, CA, CB, sq, out, Kp, nF)));
     LAUNCHED("k_coef_mix");
-    ++g_launches;
     return FST_OK;
   }
   fst_status coef_lowrank(const CoefArgs<float> &a) override { return coef_lowrank_t(a); }

@@ -422,3 +422,187 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
 }
 
 }  // namespace fst
+
+namespace fst {
+
+// ---------------------------------------------------------------------------
+// Standalone rank-r correction for the FP32 four-step path with P > 32 (and any
+// layout without the register column passes): the same tensor-core products as the
+// fast column kernels, on contiguous row blocks of CORR_ROWS samples:
+//   k_corr_c : partial S_T^T y per (pair group, row block)   (before pass C)
+//   k_corr_z : out += S_T (D o c) per (pair group, row block) (after pass C)
+// ---------------------------------------------------------------------------
+
+
+template <typename T> __device__ __forceinline__ void add_pair(const ConvArgs<T> &a, int64_t pl, int64_t n, c2<T> z) {
+  const int64_t p = a.pair0 + pl;
+  if (a.cplx) {
+    c2<T> *o = reinterpret_cast<c2<T> *>(a.out) + p * a.ld + n;
+    c2<T> v = *o;
+    v.x += z.x;
+    v.y += z.y;
+    *o = v;
+    return;
+  }
+  const int64_t s0 = 2 * p, s1 = 2 * p + 1;
+  a.out[s0 * a.ld + n] += z.x;
+  if (s1 < a.batch) a.out[s1 * a.ld + n] += z.y;
+}
+
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_corr_c(const FastArgs f) {
+  const ConvArgs<float> &a = f.a;
+  __shared__ __align__(16) float yt[2 * FAST_G * YT_STRIDE];
+  __shared__ float red[FAST_G][2 * FAST_G][8 * 3 + 1];
+  const int nK = (int)((a.N + CORR_ROWS - 1) / CORR_ROWS);
+  const int64_t blk = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
+  const int64_t n0 = blk * CORR_ROWS;
+  // signal-major tile: yt[s][k] = signal s (pair s/2, part s%2) at sample n0 + k
+  for (int e = threadIdx.x; e < FAST_G * CORR_ROWS; e += FAST_THREADS) {
+    const int g = e / CORR_ROWS, k = e % CORR_ROWS;
+    const int64_t n = n0 + k;
+    float2 v = make_float2(0.f, 0.f);
+    if (g0 + g < a.npairs && n < a.N) v = load_pair(a, g0 + g, n);
+    yt[(2 * g) * YT_STRIDE + k] = v.x;
+    yt[(2 * g + 1) * YT_STRIDE + k] = v.y;
+  }
+  __syncthreads();
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int nk = CORR_ROWS / FAST_G;   // 64 rows per warp
+  const int ntj = a.rpad / 8;
+  for (int jt0 = 0; jt0 < ntj; jt0 += 3) {
+    float acc[3][4];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < CORR_ROWS / FAST_G / 8; ++ks) {
+      const int k0 = g * nk + ks * 8;
+      uint32_t ahi[4], alo[4];
+      split_tf32(yt[gid * YT_STRIDE + k0 + tig], ahi[0], alo[0]);
+      split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig], ahi[1], alo[1]);
+      split_tf32(yt[gid * YT_STRIDE + k0 + tig + 4], ahi[2], alo[2]);
+      split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig + 4], ahi[3], alo[3]);
+      const int64_t nA = n0 + k0 + tig, nB = nA + 4;
+      const bool okA = nA < a.N, okB = nB < a.N;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int jt = jt0 + t;
+        if (jt < ntj) {
+          const int j = jt * 8 + gid;
+          uint32_t bhi[2], blo[2];
+          bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
+          blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
+          bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
+          blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
+          mma3(acc[t], ahi, alo, bhi, blo);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      red[g][gid][t * 8 + 2 * tig] = acc[t][0];
+      red[g][gid][t * 8 + 2 * tig + 1] = acc[t][1];
+      red[g][gid + 8][t * 8 + 2 * tig] = acc[t][2];
+      red[g][gid + 8][t * 8 + 2 * tig + 1] = acc[t][3];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * FAST_G * 24; t += FAST_THREADS) {
+      const int s = t / 24, jj = t % 24;
+      const int j = jt0 * 8 + jj, gp = s >> 1;
+      if (j < a.r && g0 + gp < a.npairs) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < FAST_G; ++w) sum += red[w][s][jj];
+        a.part[(((g0 + gp) * nK + blk) * 2 + (s & 1)) * a.rpad + j] = sum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// a[pair][c][j] = D_j * sum over row blocks of the partials (fixed order)
+__global__ void k_corr_reduce(const ConvArgs<float> a) {
+  const int nK = (int)((a.N + CORR_ROWS - 1) / CORR_ROWS);
+  const int64_t pl = blockIdx.x;
+  for (int t = threadIdx.x; t < 2 * a.r; t += blockDim.x) {
+    const int c = t / a.r, j = t % a.r;
+    float s = 0.f;
+    for (int b = 0; b < nK; ++b) s += a.part[((pl * nK + b) * 2 + c) * a.rpad + j];
+    a.acoef[(pl * 2 + c) * a.rpad + j] = __ldg(a.D + j) * s;
+  }
+}
+
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_corr_z(const FastArgs f) {
+  const ConvArgs<float> &a = f.a;
+  __shared__ __align__(16) float zt[CORR_ROWS][2 * FAST_G + 1];
+  __shared__ float acs[2][32][2 * FAST_G + 1];
+  const int64_t blk = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
+  const int64_t n0 = blk * CORR_ROWS;
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int ntj = a.rpad / 8;
+  for (int jt0 = 0; jt0 < ntj; jt0 += 4) {
+    for (int t = threadIdx.x; t < 32 * 2 * FAST_G; t += FAST_THREADS) {
+      const int jj = t / (2 * FAST_G), s = t % (2 * FAST_G);
+      const int j = jt0 * 8 + jj, gp = s >> 1;
+      float val = 0.f;
+      if (j < a.r && g0 + gp < a.npairs) val = a.acoef[((g0 + gp) * 2 + (s & 1)) * a.rpad + j];
+      uint32_t hi, lo;
+      split_tf32(val, hi, lo);
+      acs[0][jj][s] = __uint_as_float(hi);
+      acs[1][jj][s] = __uint_as_float(lo);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mi = 0; mi < CORR_ROWS / 16 / FAST_G; ++mi) {
+      const int mt = g + FAST_G * mi;
+      float acc[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+      const int nl0 = mt * 16 + gid, nl1 = nl0 + 8;
+      const int64_t nA = n0 + nl0, nB = n0 + nl1;
+      const bool okA = nA < a.N, okB = nB < a.N;
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) {
+        const int jt = jt0 + kt;
+        if (jt < ntj) {
+          const int j0 = jt * 8 + tig, j1 = j0 + 4;
+          uint32_t ahi[4], alo[4];
+          ahi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j0)) : 0u;
+          ahi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j0)) : 0u;
+          ahi[2] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j1)) : 0u;
+          ahi[3] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j1)) : 0u;
+          alo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j0)) : 0u;
+          alo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j0)) : 0u;
+          alo[2] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j1)) : 0u;
+          alo[3] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j1)) : 0u;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint32_t bhi[2], blo[2];
+            bhi[0] = __float_as_uint(acs[0][kt * 8 + tig][u * 8 + gid]);
+            bhi[1] = __float_as_uint(acs[0][kt * 8 + tig + 4][u * 8 + gid]);
+            blo[0] = __float_as_uint(acs[1][kt * 8 + tig][u * 8 + gid]);
+            blo[1] = __float_as_uint(acs[1][kt * 8 + tig + 4][u * 8 + gid]);
+            mma3(acc[u], ahi, alo, bhi, blo);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const bool first = (jt0 == 0);
+        float *z0 = &zt[nl0][u * 8 + 2 * tig], *z1 = &zt[nl1][u * 8 + 2 * tig];
+        z0[0] = (first ? 0.f : z0[0]) + acc[u][0];
+        z0[1] = (first ? 0.f : z0[1]) + acc[u][1];
+        z1[0] = (first ? 0.f : z1[0]) + acc[u][2];
+        z1[1] = (first ? 0.f : z1[1]) + acc[u][3];
+      }
+    }
+    __syncthreads();
+  }
+  // out += Z, coalesced along the samples of each signal
+  for (int e = threadIdx.x; e < FAST_G * CORR_ROWS; e += FAST_THREADS) {
+    const int gp = e / CORR_ROWS, k = e % CORR_ROWS;
+    const int64_t n = n0 + k;
+    if (g0 + gp < a.npairs && n < a.N) add_pair(a, g0 + gp, n, make_float2(zt[k][2 * gp], zt[k][2 * gp + 1]));
+  }
+}
+
+}  // namespace fst

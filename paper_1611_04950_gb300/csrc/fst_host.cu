@@ -81,6 +81,7 @@ Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast) {
     L.smem_A = L.smem_C = 0;
     L.fused_reduce = (L.log2Q == 12);
   } else {
+    L.split_corr = allow_fast && !dbl;
     const int tile = 8192;
     const int ncols = std::max(1, tile / P);
     const int nb0 = std::min(32, ncols);
@@ -103,7 +104,10 @@ static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
   const int64_t M = 1LL << L.log2M;
   if (L.small) return forward ? (size_t)L.chunk * M * cs : 0;
   size_t b = (size_t)L.chunk * M * cs;
-  b += (size_t)L.chunk * L.ntiles * 2 * std::max(rpad, 1) * rs;
+  // partial sums: per column tile (in-pass correction) or per row block of
+  // CORR_ROWS samples of the M/2 >= N possible ones (separate correction)
+  const int64_t nparts = std::max<int64_t>(L.ntiles, (M / 2 + CORR_ROWS - 1) / CORR_ROWS);
+  b += (size_t)L.chunk * nparts * 2 * std::max(rpad, 1) * rs;
   b += (size_t)L.chunk * 2 * std::max(rpad, 1) * rs;
   return b + 1024;
 }
@@ -136,13 +140,24 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     a.inter = (C *)w;
     if (!L.small) {
       const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
+      const int64_t nparts = std::max<int64_t>(L.ntiles, (M / 2 + CORR_ROWS - 1) / CORR_ROWS);
       a.part = (T *)(w + inter_b);
-      a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
+      a.acoef = (T *)(w + inter_b + (size_t)L.chunk * nparts * 2 * std::max(a.rpad, 1) * sizeof(T));
     }
     a.pair0 = p0;
     a.npairs = std::min<int64_t>(L.chunk, npairs - p0);
     if (L.small) {
       TRY(R->small(a, L));
+    } else if (L.split_corr && a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device()) {
+      const ConvArgs<float> &af = *reinterpret_cast<const ConvArgs<float> *>(&a);
+      ConvArgs<T> b = a;
+      b.mode = MODE_CONV;
+      TRY(R->corr_c(af));
+      TRY(R->corr_reduce(af));
+      TRY(R->passA(b, L));
+      TRY(R->passB(b, L));
+      TRY(R->passC(b, L));
+      TRY(R->corr_z(af));
     } else {
       TRY(R->passA(a, L));
       if (a.mode == MODE_FULL && a.r > 0 && !(L.fused_reduce && R->device())) TRY(R->reduce(a, L));
@@ -964,7 +979,7 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
   Layout Lf = make_layout(N, log2N, dbl, 0, false);
   if (!Lf.small) Lf.Pnz = 1 << Lf.log2P;
   const int64_t npairs = cplx ? batch : (batch + 1) / 2;
-  const size_t ws_f = (size_t)Lf.chunk * N * sizeof(C) + (size_t)Lf.chunk * std::max(Lf.ntiles, 1) * 2 * sizeof(T) * 8 + 4096;
+  const size_t ws_f = ws_need(Lf, dbl, 0, true) + 4096;
   const int nchunks = (int)((N + COEF_CHUNK - 1) / COEF_CHUNK);
   const size_t part_b = (size_t)batch * nchunks * cp->nraw * 2 * sizeof(T);
   const size_t partU_b = (size_t)batch * nchunks * std::max<int64_t>(p->r, 1) * 2 * sizeof(T);

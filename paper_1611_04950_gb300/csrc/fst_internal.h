@@ -53,6 +53,10 @@ struct Runner {
   virtual fst_status passB(const ConvArgs<double> &a, const Layout &L) = 0;
   virtual fst_status passC(const ConvArgs<float> &a, const Layout &L) = 0;
   virtual fst_status passC(const ConvArgs<double> &a, const Layout &L) = 0;
+  // separate correction (FP32, device): partials, reduce to a = D o c, out += S_T a
+  virtual fst_status corr_c(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  virtual fst_status corr_reduce(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  virtual fst_status corr_z(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
 
   // plan kernels (all pointers in runner memory)
   virtual fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo,
