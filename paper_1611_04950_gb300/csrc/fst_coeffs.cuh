@@ -41,6 +41,8 @@ template <typename T> struct CoefArgs {
   const T *ST;       // [N][rpad]
   int r, rpad;
   T *partU;          // [batch][nchunks][r][2]
+  int upairs;        // 1: U2^* y already reduced per pair in acoefU ([pair][re/im][rpad])
+  const T *acoefU;
 };
 
 template <typename T> struct CState {
@@ -71,7 +73,9 @@ FST_HD void coef_block_reduce(Ex &ex, T *red, int cnt, T *dst) {
   using St = typename Ex::State;
   const int nthr = ex.nthr;
   ex.phase([&](int tid, St &st) {
-    for (int q = 0; q < 2 * cnt; ++q) red[q * nthr + tid] = st.acc[q];
+#pragma unroll
+    for (int q = 0; q < 2 * COEF_GROUP; ++q)
+      if (q < 2 * cnt) red[q * nthr + tid] = st.acc[q];
   });
   ex.phase([&](int tid, St &) {
     // thread (q, part): 8 parts of nthr / 8 values each, then the parts in order
@@ -111,6 +115,7 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
     int obase = vbase[variant];
     // v(n) = phase(n) y(n) with phase = exp(-j..) (conjph: exp(+j..)); reset recurrences
     ex.phase([&](int tid, St &st) {
+#pragma unroll
       for (int e = 0; e < COEF_E; ++e) {
         const int64_t n = n0 + tid + (int64_t)e * nthr;
         c2<T> v = mk<T>(0, 0);
@@ -134,9 +139,13 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
       for (int k0 = 0; k0 < a.rH; k0 += COEF_GROUP / 2) {
         const int kc = (a.rH - k0 < COEF_GROUP / 2) ? a.rH - k0 : COEF_GROUP / 2;
         ex.phase([&](int tid, St &st) {
+#pragma unroll
           for (int q = 0; q < 2 * COEF_GROUP; ++q) st.acc[q] = 0;
-          for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+          for (int kk = 0; kk < COEF_GROUP / 2; ++kk) {
+            if (kk >= kc) break;
             const int k = k0 + kk;
+#pragma unroll
             for (int e = 0; e < COEF_E; ++e) {
               const int64_t n = n0 + tid + (int64_t)e * nthr;
               if (k > 0 && n < a.N) {
@@ -174,8 +183,12 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
     for (int i0 = 0; i0 < D; i0 += COEF_GROUP) {
       const int ic = (D - i0 < COEF_GROUP) ? D - i0 : COEF_GROUP;
       ex.phase([&](int tid, St &st) {
+#pragma unroll
         for (int q = 0; q < 2 * COEF_GROUP; ++q) st.acc[q] = 0;
-        for (int ii = 0; ii < ic; ++ii) {
+#pragma unroll
+        for (int ii = 0; ii < COEF_GROUP; ++ii) {
+          if (ii >= ic) break;
+#pragma unroll
           for (int e = 0; e < COEF_E; ++e) {
             const int64_t n = n0 + tid + (int64_t)e * nthr;
             const T u = ((T)n - cen) * invN;
@@ -286,7 +299,7 @@ FST_HD void coef_reduce_body(const T *part, int nchunks, int nout, int64_t sig, 
 // final L2^* y and U2^* y entries (index o in [0, r1 + r)) from the raw totals
 template <typename T>
 FST_HD c2<T> coef_mix_value(const CoefArgs<T> &a, const T *raw, const T *rawU, const T *CA, const T *CB,
-                            const T *sqrtD, int o) {
+                            const T *sqrtD, int o, int64_t sig) {
   const int rH = a.rH, DA = a.DA, DB = a.DB;
   auto R = [&](int i) { return mk<T>(raw[2 * i], raw[2 * i + 1]); };
   const int r1 = 4 * rH + 2 * DA + 2 * DB;
@@ -310,6 +323,11 @@ FST_HD c2<T> coef_mix_value(const CoefArgs<T> &a, const T *raw, const T *rawU, c
     return mk<T>(sr, si);
   }
   const int j = o - r1;
+  if (a.upairs) {
+    // sqrt|D| already applied; real pairs hold signals 2p (re part) and 2p+1 (im part)
+    if (a.cplx) return mk<T>(a.acoefU[(sig * 2) * a.rpad + j], a.acoefU[(sig * 2 + 1) * a.rpad + j]);
+    return mk<T>(a.acoefU[((sig / 2) * 2 + (sig & 1)) * a.rpad + j], (T)0);
+  }
   return mk<T>(sqrtD[j] * rawU[2 * j], sqrtD[j] * rawU[2 * j + 1]);
 }
 

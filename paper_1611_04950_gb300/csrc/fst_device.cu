@@ -186,7 +186,7 @@ __global__ void k_coef_mix(const CoefArgs<T> a, const T *tot, const T *totU, con
   const int nfin = 4 * a.rH + 2 * a.DA + 2 * a.DB + a.r;
   if (o >= nfin) return;
   out[sig * Kp + nF + o] =
-      coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2, totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o);
+      coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2, totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o, sig);
 }
 
 __global__ void k_split_tf32(const float *src, float *hi, float *lo, int64_t n) {
@@ -440,14 +440,13 @@ struct DevRunner : Runner {
   fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
   fst_status corr_c(const ConvArgs<float> &a) override {
     FastArgs f{a, a.ST_hi, a.ST_lo};
-    dim3 grid((unsigned)((a.N + CORR_ROWS - 1) / CORR_ROWS), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
+    dim3 grid((unsigned)((a.N + CORR_BLOCK - 1) / CORR_BLOCK), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     PROF("k_corr_c", a.npairs, (k_corr_c<<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_corr_c");
     return FST_OK;
   }
-  fst_status corr_reduce(const ConvArgs<float> &a) override {
-    const int thr = std::min(1024, std::max(32, ((2 * a.r + 31) / 32) * 32));
-    PROF("k_corr_reduce", a.npairs, (k_corr_reduce<<<(unsigned)a.npairs, thr, 0, cur>>>(a)));
+  fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) override {
+    PROF("k_corr_reduce", a.npairs, (k_corr_reduce<<<(unsigned)a.npairs, 256, 0, cur>>>(a, scale)));
     LAUNCHED("k_corr_reduce");
     return FST_OK;
   }

@@ -201,7 +201,7 @@ struct EmuRunner : Runner {
     for (int64_t sig = 0; sig < a.batch; ++sig)
       for (int o = 0; o < nfin; ++o)
         out[sig * Kp + nF + o] = coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2,
-                                                    totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o);
+                                                    totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o, sig);
     return FST_OK;
   }
   fst_status coef_lowrank(const CoefArgs<float> &a) override { return coef_lowrank_t(a); }

@@ -449,85 +449,99 @@ template <typename T> __device__ __forceinline__ void add_pair(const ConvArgs<T>
   if (s1 < a.batch) a.out[s1 * a.ld + n] += z.y;
 }
 
-__global__ void __launch_bounds__(FAST_THREADS, 3) k_corr_c(const FastArgs f) {
+__global__ void __launch_bounds__(FAST_THREADS, 2) k_corr_c(const FastArgs f) {
   const ConvArgs<float> &a = f.a;
-  __shared__ __align__(16) float yt[2 * FAST_G * YT_STRIDE];
-  __shared__ float red[FAST_G][2 * FAST_G][8 * 3 + 1];
-  const int nK = (int)((a.N + CORR_ROWS - 1) / CORR_ROWS);
+  // one buffer: the signal-major tile during the products, the per-warp results after
+  constexpr int RED_STRIDE = 65;
+  constexpr int BUF = (2 * FAST_G * YT_STRIDE > FAST_G * 2 * FAST_G * RED_STRIDE) ? 2 * FAST_G * YT_STRIDE
+                                                                                  : FAST_G * 2 * FAST_G * RED_STRIDE;
+  __shared__ __align__(16) float buf[BUF];
+  float *yt = buf;
+  const int nK = (int)((a.N + CORR_BLOCK - 1) / CORR_BLOCK);
   const int64_t blk = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
-  const int64_t n0 = blk * CORR_ROWS;
-  // signal-major tile: yt[s][k] = signal s (pair s/2, part s%2) at sample n0 + k
-  for (int e = threadIdx.x; e < FAST_G * CORR_ROWS; e += FAST_THREADS) {
-    const int g = e / CORR_ROWS, k = e % CORR_ROWS;
-    const int64_t n = n0 + k;
-    float2 v = make_float2(0.f, 0.f);
-    if (g0 + g < a.npairs && n < a.N) v = load_pair(a, g0 + g, n);
-    yt[(2 * g) * YT_STRIDE + k] = v.x;
-    yt[(2 * g + 1) * YT_STRIDE + k] = v.y;
-  }
-  __syncthreads();
   const int g = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
-  const int nk = CORR_ROWS / FAST_G;   // 64 rows per warp
+  const int nk = CORR_ROWS / FAST_G;   // 64 rows per warp and tile
   const int ntj = a.rpad / 8;
-  for (int jt0 = 0; jt0 < ntj; jt0 += 3) {
-    float acc[3][4];
+  for (int jt0 = 0; jt0 < ntj; jt0 += 8) {
+    float acc[8][4];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    for (int t = 0; t < 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    for (int sub = 0; sub < CORR_BLOCK / CORR_ROWS; ++sub) {
+      const int64_t n0 = blk * CORR_BLOCK + (int64_t)sub * CORR_ROWS;
+      __syncthreads();
+      // yt[s][k] = signal s (pair s/2, part s%2) at sample n0 + k
+      for (int e = threadIdx.x; e < FAST_G * CORR_ROWS; e += FAST_THREADS) {
+        const int gg = e / CORR_ROWS, k = e % CORR_ROWS;
+        const int64_t n = n0 + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (g0 + gg < a.npairs && n < a.N) v = load_pair(a, g0 + gg, n);
+        yt[(2 * gg) * YT_STRIDE + k] = v.x;
+        yt[(2 * gg + 1) * YT_STRIDE + k] = v.y;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int ks = 0; ks < nk / 8; ++ks) {
+        const int k0 = g * nk + ks * 8;
+        uint32_t ahi[4], alo[4];
+        split_tf32(yt[gid * YT_STRIDE + k0 + tig], ahi[0], alo[0]);
+        split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig], ahi[1], alo[1]);
+        split_tf32(yt[gid * YT_STRIDE + k0 + tig + 4], ahi[2], alo[2]);
+        split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig + 4], ahi[3], alo[3]);
+        const int64_t nA = n0 + k0 + tig, nB = nA + 4;
+        const bool okA = nA < a.N, okB = nB < a.N;
 #pragma unroll
-    for (int ks = 0; ks < CORR_ROWS / FAST_G / 8; ++ks) {
-      const int k0 = g * nk + ks * 8;
-      uint32_t ahi[4], alo[4];
-      split_tf32(yt[gid * YT_STRIDE + k0 + tig], ahi[0], alo[0]);
-      split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig], ahi[1], alo[1]);
-      split_tf32(yt[gid * YT_STRIDE + k0 + tig + 4], ahi[2], alo[2]);
-      split_tf32(yt[(gid + 8) * YT_STRIDE + k0 + tig + 4], ahi[3], alo[3]);
-      const int64_t nA = n0 + k0 + tig, nB = nA + 4;
-      const bool okA = nA < a.N, okB = nB < a.N;
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int jt = jt0 + t;
-        if (jt < ntj) {
-          const int j = jt * 8 + gid;
-          uint32_t bhi[2], blo[2];
-          bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
-          blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
-          bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
-          blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
-          mma3(acc[t], ahi, alo, bhi, blo);
+        for (int t = 0; t < 8; ++t) {
+          const int jt = jt0 + t;
+          if (jt < ntj) {
+            const int j = jt * 8 + gid;
+            uint32_t bhi[2], blo[2];
+            bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
+            blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
+            bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
+            blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
+            mma3(acc[t], ahi, alo, bhi, blo);
+          }
         }
       }
     }
+    __syncthreads();
+    float *red = buf;   // [warp][signal][64 j]
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      red[g][gid][t * 8 + 2 * tig] = acc[t][0];
-      red[g][gid][t * 8 + 2 * tig + 1] = acc[t][1];
-      red[g][gid + 8][t * 8 + 2 * tig] = acc[t][2];
-      red[g][gid + 8][t * 8 + 2 * tig + 1] = acc[t][3];
+    for (int t = 0; t < 8; ++t) {
+      float *r0 = red + (g * 2 * FAST_G + gid) * RED_STRIDE + t * 8 + 2 * tig;
+      float *r1 = red + (g * 2 * FAST_G + gid + 8) * RED_STRIDE + t * 8 + 2 * tig;
+      r0[0] = acc[t][0];
+      r0[1] = acc[t][1];
+      r1[0] = acc[t][2];
+      r1[1] = acc[t][3];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * FAST_G * 24; t += FAST_THREADS) {
-      const int s = t / 24, jj = t % 24;
-      const int j = jt0 * 8 + jj, gp = s >> 1;
+    for (int t = threadIdx.x; t < 2 * FAST_G * 64; t += FAST_THREADS) {
+      const int sgl = t / 64, jj = t % 64;
+      const int j = jt0 * 8 + jj, gp = sgl >> 1;
       if (j < a.r && g0 + gp < a.npairs) {
         float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < FAST_G; ++w) sum += red[w][s][jj];
-        a.part[(((g0 + gp) * nK + blk) * 2 + (s & 1)) * a.rpad + j] = sum;
+        for (int w = 0; w < FAST_G; ++w) sum += red[(w * 2 * FAST_G + sgl) * RED_STRIDE + jj];
+        a.part[(((g0 + gp) * nK + blk) * 2 + (sgl & 1)) * a.rpad + j] = sum;
       }
     }
-    __syncthreads();
   }
 }
 
-// a[pair][c][j] = D_j * sum over row blocks of the partials (fixed order)
-__global__ void k_corr_reduce(const ConvArgs<float> a) {
-  const int nK = (int)((a.N + CORR_ROWS - 1) / CORR_ROWS);
+// a[pair][c][j] = scale_j * sum over row blocks of the partials: warp per output,
+// lanes stride the blocks, fixed xor-tree across lanes (deterministic)
+__global__ void k_corr_reduce(const ConvArgs<float> a, const float *scale) {
+  const int nK = (int)((a.N + CORR_BLOCK - 1) / CORR_BLOCK);
   const int64_t pl = blockIdx.x;
-  for (int t = threadIdx.x; t < 2 * a.r; t += blockDim.x) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = w; t < 2 * a.r; t += nw) {
     const int c = t / a.r, j = t % a.r;
     float s = 0.f;
-    for (int b = 0; b < nK; ++b) s += a.part[((pl * nK + b) * 2 + c) * a.rpad + j];
-    a.acoef[(pl * 2 + c) * a.rpad + j] = __ldg(a.D + j) * s;
+    for (int b = lane; b < nK; b += 32) s += a.part[((pl * nK + b) * 2 + c) * a.rpad + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) a.acoef[(pl * 2 + c) * a.rpad + j] = __ldg(scale + j) * s;
   }
 }
 

@@ -104,10 +104,7 @@ static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
   const int64_t M = 1LL << L.log2M;
   if (L.small) return forward ? (size_t)L.chunk * M * cs : 0;
   size_t b = (size_t)L.chunk * M * cs;
-  // partial sums: per column tile (in-pass correction) or per row block of
-  // CORR_ROWS samples of the M/2 >= N possible ones (separate correction)
-  const int64_t nparts = std::max<int64_t>(L.ntiles, (M / 2 + CORR_ROWS - 1) / CORR_ROWS);
-  b += (size_t)L.chunk * nparts * 2 * std::max(rpad, 1) * rs;
+  b += (size_t)L.chunk * L.ntiles * 2 * std::max(rpad, 1) * rs;
   b += (size_t)L.chunk * 2 * std::max(rpad, 1) * rs;
   return b + 1024;
 }
@@ -118,6 +115,12 @@ static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
 
 // bytes of one launch group's scratch (one lane)
 static size_t slot_bytes(const Layout &L, bool dbl, int rpad, bool forward) { return ws_need(L, dbl, rpad, forward); }
+
+// scratch of the separate correction for npairs pairs (partials per CORR_BLOCK + a)
+static size_t split_corr_bytes(int64_t N, int64_t npairs, int rpad) {
+  const int64_t nK = (N + CORR_BLOCK - 1) / CORR_BLOCK;
+  return (size_t)npairs * (nK + 1) * 2 * std::max(rpad, 1) * sizeof(float) + 256;
+}
 
 template <typename T>
 static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t npairs, void *ws) {
@@ -132,6 +135,22 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   const int64_t M = 1LL << L.log2M;
   const int lanes = R->lanes();
   const size_t slot = slot_bytes(L, sizeof(T) == 8, a.rpad, a.mode == MODE_FORWARD);
+  // separate tensor-core correction (FP32 device, P > 32): S_T^T y over every pair
+  // first (before any output is written, so y == out works), out += S_T a at the end
+  const bool split = L.split_corr && a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device();
+  ConvArgs<float> sc{};
+  if (split) {
+    sc = *reinterpret_cast<const ConvArgs<float> *>(&a);
+    char *w = (char *)ws + (size_t)lanes * slot;
+    const int64_t nK = (a.N + CORR_BLOCK - 1) / CORR_BLOCK;
+    sc.pair0 = 0;
+    sc.npairs = npairs;
+    sc.part = (float *)w;
+    sc.acoef = (float *)(w + (size_t)npairs * nK * 2 * a.rpad * sizeof(float));
+    TRY(R->corr_c(sc));
+    TRY(R->corr_reduce(sc, (const float *)a.D));
+    a.mode = MODE_CONV;
+  }
   int64_t group = 0;
   for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk, ++group) {
     const int lane = (int)(group % lanes);
@@ -140,24 +159,13 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     a.inter = (C *)w;
     if (!L.small) {
       const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
-      const int64_t nparts = std::max<int64_t>(L.ntiles, (M / 2 + CORR_ROWS - 1) / CORR_ROWS);
       a.part = (T *)(w + inter_b);
-      a.acoef = (T *)(w + inter_b + (size_t)L.chunk * nparts * 2 * std::max(a.rpad, 1) * sizeof(T));
+      a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
     }
     a.pair0 = p0;
     a.npairs = std::min<int64_t>(L.chunk, npairs - p0);
     if (L.small) {
       TRY(R->small(a, L));
-    } else if (L.split_corr && a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device()) {
-      const ConvArgs<float> &af = *reinterpret_cast<const ConvArgs<float> *>(&a);
-      ConvArgs<T> b = a;
-      b.mode = MODE_CONV;
-      TRY(R->corr_c(af));
-      TRY(R->corr_reduce(af));
-      TRY(R->passA(b, L));
-      TRY(R->passB(b, L));
-      TRY(R->passC(b, L));
-      TRY(R->corr_z(af));
     } else {
       TRY(R->passA(a, L));
       if (a.mode == MODE_FULL && a.r > 0 && !(L.fused_reduce && R->device())) TRY(R->reduce(a, L));
@@ -166,6 +174,7 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     }
   }
   R->use_lane(0);
+  if (split) TRY(R->corr_z(sc));
   return FST_OK;
 }
 
@@ -215,12 +224,13 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.mode = full ? MODE_FULL : MODE_CONV;
   const int64_t npairs = cplx ? batch : (batch + 1) / 2;
   const bool dbl = sizeof(T) == 8;
+  const size_t extra = (L0.split_corr && full && p->r > 0) ? split_corr_bytes(p->N, npairs, (int)p->rpad) : 0;
   if (!ext_ws) {
     Runner *R = p->R;
     const size_t slot = ws_need(L0, dbl, (int)p->rpad, false);
     const bool graphs = R->device() && graphs_enabled() && !profiling_enabled() && !R->user_stream_capturing();
     if (!graphs) {
-      TRY(ensure_ws(p, slot));
+      TRY(ensure_ws(p, slot + extra));
       return run_conv<T>(R, L0, a, npairs, p->ws);
     }
     // whole apply as one cached CUDA graph (two overlapping lanes of launch groups)
@@ -228,7 +238,7 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
       if (e.y == (const void *)y && e.out == (void *)out && e.batch == batch && e.ld == ld &&
           e.dtype == (int)(cplx ? 1 : 0) + (dbl ? 2 : 0) && e.full == full)
         return R->graph_launch(e.exec, e.nodes);
-    TRY(ensure_ws(p, 2 * slot + 256));
+    TRY(ensure_ws(p, 2 * slot + 256 + extra));
     if (!R->graph_begin()) {
       return run_conv<T>(R, L0, a, npairs, p->ws);
     }
@@ -255,11 +265,11 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
     int64_t ch = L.chunk;
     while (ch > L.G) {
       L.chunk = ch;
-      if (ws_need(L, dbl, (int)p->rpad, false) <= ext_bytes) break;
+      if (ws_need(L, dbl, (int)p->rpad, false) + extra <= ext_bytes) break;
       ch = std::max<int64_t>(L.G, ((ch / 2) / L.G) * L.G);
     }
     L.chunk = ch;
-    if (ws_need(L, dbl, (int)p->rpad, false) > ext_bytes)
+    if (ws_need(L, dbl, (int)p->rpad, false) + extra > ext_bytes)
       return fail(FST_EINVAL, "signal too long for the fixed scratch buffer");
   }
   return run_conv<T>(p->R, L, a, npairs, ext_ws);
@@ -982,7 +992,8 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
   const size_t ws_f = ws_need(Lf, dbl, 0, true) + 4096;
   const int nchunks = (int)((N + COEF_CHUNK - 1) / COEF_CHUNK);
   const size_t part_b = (size_t)batch * nchunks * cp->nraw * 2 * sizeof(T);
-  const size_t partU_b = (size_t)batch * nchunks * std::max<int64_t>(p->r, 1) * 2 * sizeof(T);
+  const size_t partU_b = std::max((size_t)batch * nchunks * std::max<int64_t>(p->r, 1) * 2 * sizeof(T),
+                                  split_corr_bytes(N, npairs, (int)p->rpad));
   const size_t tot_b = (size_t)batch * cp->nraw * 2 * sizeof(T);
   const size_t totU_b = (size_t)batch * std::max<int64_t>(p->r, 1) * 2 * sizeof(T);
   TRY(ensure_ws(p, std::max(ws_f, part_b + partU_b + tot_b + totU_b + 4096)));
@@ -1046,9 +1057,33 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
   const T *CA, *CB, *sq;
   CoefPtrs<T>::fill(cp, c, CA, CB, sq);
   TRY(R->coef_lowrank(c));
-  if (p->r > 0) TRY(R->coef_st(c));
+  const bool mma_u = !dbl && R->device() && p->r > 0;
+  if (mma_u) {
+    // U2^* y on the tensor cores: S_T^T y per pair, scaled by sqrt|D| in the reduce
+    ConvArgs<float> ca{};
+    ca.y = (const float *)y;
+    ca.ld = ld;
+    ca.batch = batch;
+    ca.cplx = cplx ? 1 : 0;
+    ca.N = N;
+    ca.r = (int)p->r;
+    ca.rpad = (int)p->rpad;
+    ca.ST_hi = p->ST32_hi;
+    ca.ST_lo = p->ST32_lo;
+    ca.pair0 = 0;
+    ca.npairs = npairs;
+    const int64_t nK = (N + CORR_BLOCK - 1) / CORR_BLOCK;
+    ca.part = (float *)c.partU;
+    ca.acoef = (float *)c.partU + (size_t)npairs * nK * 2 * p->rpad;
+    TRY(R->corr_c(ca));
+    TRY(R->corr_reduce(ca, (const float *)sq));
+    c.upairs = 1;
+    c.acoefU = (const T *)ca.acoef;
+  } else if (p->r > 0) {
+    TRY(R->coef_st(c));
+  }
   TRY(R->coef_reduce(c.part, nchunks, cp->nraw, batch, tot));
-  if (p->r > 0) TRY(R->coef_reduce(c.partU, nchunks, (int)p->r, batch, totU));
+  if (p->r > 0 && !mma_u) TRY(R->coef_reduce(c.partU, nchunks, (int)p->r, batch, totU));
   TRY(R->coef_mix(c, tot, totU, CA, CB, sq, out, Kp, nF));
   return FST_OK;
 }

@@ -55,7 +55,7 @@ struct Runner {
   virtual fst_status passC(const ConvArgs<double> &a, const Layout &L) = 0;
   // separate correction (FP32, device): partials, reduce to a = D o c, out += S_T a
   virtual fst_status corr_c(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
-  virtual fst_status corr_reduce(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  virtual fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) { return FST_EUNSUPPORTED; }
   virtual fst_status corr_z(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
 
   // plan kernels (all pointers in runner memory)

@@ -34,7 +34,8 @@ namespace fst {
 
 enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2 };
 
-constexpr int CORR_ROWS = 512;   // samples per row block of the separate correction kernels
+constexpr int CORR_ROWS = 512;    // samples per tensor-core tile of the separate correction kernels
+constexpr int CORR_BLOCK = 2048;  // samples per partial sum of S_T^T y (four tiles)
 
 // Launch layout of the length-M transform for one real type.
 struct Layout {
