@@ -45,6 +45,9 @@ WORKLOADS = {
                 batch=64),
     "c4m": dict(desc="N=2^22 W=1/4 eps=1e-8, 16 real FP32 signals (8 N(0,1), 8 1024-tone)", batch=16),
     "tiny": dict(desc="N=4096 W=1/16 eps=1e-6, 2 real signals (N(0,1), 64-tone)", batch=2),
+    "ragged": dict(desc="ragged batch of 4096 real FP32 signals, N log-uniform in [1000, 262144], "
+                        "W ~ U[1/64, 1/4], eps in {1e-3, 1e-6, 1e-8}, N(0,1) entries; one plan per signal",
+                   batch=4096),
 }
 
 
@@ -178,6 +181,72 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_ragged_bench(args):
+    """Ragged batch: fst_plan_many (timed apart), then fst_project_ragged per step,
+    against the same signals projected by one fst_project call per signal."""
+    import numpy as np
+    import torch
+    from paper_1611_04950_gb300 import fst as F
+    from paper_1611_04950_gb300 import workloads as WL
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    count = args.batch or 4096
+    params = WL.ragged_params(count, seed=3)
+    t0 = time.perf_counter()
+    ps = F.PlanSet(params)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    ys = [torch.randn(N, device="cuda", generator=gen) for (N, W, e) in params]
+    outs = [torch.empty_like(v) for v in ys]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ps.project(ys, outs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    l0 = F.fst_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ps.project(ys, outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = F.fst_launch_count() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    total = sum(N for (N, W, e) in params)
+    # one fst_project call per signal (each plan's own cached graph)
+    def per_signal():
+        for h, y, o in zip(ps.h, ys, outs):
+            F.fst_project(h, y.data_ptr(), o.data_ptr(), 1, 0, F.FST_F32, stream.cuda_stream)
+    for _ in range(2):
+        per_signal()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(2, args.steps // 4)):
+        per_signal()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_signal = e0.elapsed_time(e1) / max(2, args.steps // 4)
+    peaks, src = measured_peaks()
+    rsum = sum(F.fst_plan_info(h)["r"] for h in ps.h)
+    alg = sum(N * 8 + N * F.fst_plan_info(h)["r"] * 4 for h, (N, W, e) in zip(ps.h, params))
+    line = {
+        "metric": "projected samples/s", "value": total / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["ragged"]["desc"], "signals": count, "samples": total,
+                   "mean_r": rsum / count, "plan_many_s": plan_s,
+                   "per_signal_launch_ms": ms_per_signal,
+                   "l2": "inputs + outputs + S_T exceed the 129 MB L2; no flush"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "whole ragged step", "peak_source": src},
+        "e2e": None, "cpu_baseline": None, "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +263,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ragged":
+        return run_ragged_bench(args)
 
     import numpy as np
     import torch

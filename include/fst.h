@@ -180,6 +180,32 @@ fst_status fst_coeffs_info(fst_plan_t plan, int64_t *Kprime, int64_t *nF, int64_
  */
 fst_status fst_adi_shifts(int64_t N, int r, double *out);
 
+/*
+ * fst_plan_many -- count plans at once (ragged batches: one plan per signal).
+ * Same precomputation as fst_plan for each (N[i], W[i], K[i] or round(2NW) when
+ * K is NULL or K[i] < 0, eps[i]), projection operator; the bisection and inverse
+ * iteration of all plans' eigen-windows run as one batch of independent targets.
+ * out[count] receives the plans (destroy each with fst_destroy).  On error every
+ * plan of the call is freed and out[] is NULL.  Synchronous.
+ */
+fst_status fst_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const double *W,
+                         const int64_t *K, const double *eps, void *stream);
+
+/*
+ * fst_project_ragged -- P_fast y_i for a ragged batch: signal i (device pointer
+ * y[i], N_i samples of plans[i]) is projected into out[i] with its own plan.
+ * Signals whose transform fits one CTA (FP32 N <= 8192, FP64 N <= 4096) go through
+ * one launch per FFT length with per-signal descriptors; longer ones through their
+ * plan's four-step path.  The first call with a given (plans, y, out, dtype)
+ * signature runs directly and allocates; the second records the whole batch in a
+ * CUDA graph on a private stream; later calls replay it on `stream` (set
+ * FST_GRAPHS=0 in the environment to always launch directly).  Calls with
+ * different signatures keep up to four recorded batches.
+ * Errors: FST_EINVAL (NULL pointers, count < 0), FST_ENOMEM, FST_ECUDA.
+ */
+fst_status fst_project_ragged(const fst_plan_t *plans, const void *const *y, void *const *out,
+                              int64_t count, int dtype, void *stream);
+
 /* fst_destroy -- frees the plan and its device memory.  NULL-safe. */
 fst_status fst_destroy(fst_plan_t plan);
 

@@ -20,6 +20,10 @@ extern "C" {
 /* as fst_plan_op, executed by the host emulator.  Same argument rules and errors. */
 fst_status fst_emu_plan_op(fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op, double alpha);
 
+/* as fst_plan_many, executed by the host emulator. */
+fst_status fst_emu_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const double *W,
+                             const int64_t *K, const double *eps);
+
 /* 1 if the plan runs on the host emulator, 0 otherwise (including NULL). */
 int fst_plan_is_emulated(fst_plan_t plan);
 

@@ -68,6 +68,28 @@ template <typename T> __global__ void __launch_bounds__(1024) k_small(const Conv
   small_body<T>(ex, a, (int64_t)blockIdx.x, buf, red, coef);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) k_small_ragged(const RaggedDesc<T> *d, const ConvArgs<T> base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = 1 << base.log2M;
+  c2<T> *buf = reinterpret_cast<c2<T> *>(smem);
+  T *red = reinterpret_cast<T *>(smem + padded_size(L) * sizeof(c2<T>));
+  T *coef = red + ((blockDim.x + 31) / 32) * 128;
+  const RaggedDesc<T> q = d[blockIdx.x];
+  ConvArgs<T> a = base;
+  a.y = q.y;
+  a.out = q.out;
+  a.ld = q.N;
+  a.N = q.N;
+  a.spec = q.spec;
+  a.ST = q.ST;
+  a.D = q.D;
+  a.r = q.r;
+  a.rpad = q.rpad;
+  DevEx<T> ex;
+  small_body<T>(ex, a, 0, buf, red, coef);
+}
+
 template <typename T> __global__ void __launch_bounds__(1024) k_passA(const ConvArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int P = 1 << a.log2P;
@@ -118,6 +140,29 @@ __global__ void k_finalize(const double *x, int n, int nt, int parity, int64_t N
   __shared__ double sh[2 * 256];
   DevExPlan ex;
   finalize_body(ex, x, n, nt, (int)blockIdx.x, parity, N, S + (int64_t)blockIdx.x * N, sh);
+}
+
+__global__ void k_bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
+                              int *flag) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const TargetDesc q = td[t];
+  bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag);
+}
+__global__ void k_invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat,
+                             const double *theta, double *x, double *fd, double *fdl, double *fdu, double *fdu2,
+                             uint8_t *piv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const TargetDesc q = td[t];
+  invit_body(dcat + q.mat_off, ecat + q.mat_off, q.n, theta[t], q.tol, 3, 0, 1, x + q.x_off, fd + q.x_off,
+             fdl + q.x_off, fdu + q.x_off, fdu2 + q.x_off, piv + q.x_off);
+}
+__global__ void k_finalize_many(const TargetDesc *td, const double *x) {
+  __shared__ double sh[2 * 256];
+  DevExPlan ex;
+  const TargetDesc q = td[blockIdx.x];
+  finalize_body(ex, x + q.x_off, q.n, 1, 0, q.parity, q.N, q.S, sh);
 }
 
 __global__ void k_dot(const double *a, const double *b, int64_t N, double *out) {
@@ -223,6 +268,8 @@ static fst_status set_attrs() {
   const int mx = 227 * 1024;
   CU(cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_small_ragged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_small_ragged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passA<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passA<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passB<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
@@ -414,6 +461,18 @@ struct DevRunner : Runner {
     LAUNCHED("k_passC");
     return FST_OK;
   }
+  template <typename T>
+  fst_status small_ragged_t(const RaggedDesc<T> *d, int count, const ConvArgs<T> &base, const Layout &L) {
+    if (set_attrs() != FST_OK) return FST_ECUDA;
+    PROF(sizeof(T) == 4 ? "k_small_ragged<f32>" : "k_small_ragged<f64>", count,
+         (k_small_ragged<T><<<(unsigned)count, L.nthr_small, L.smem_small, cur>>>(d, base)));
+    LAUNCHED("k_small_ragged");
+    return FST_OK;
+  }
+  fst_status small_ragged(const RaggedDesc<float> *d, int count, const ConvArgs<float> &base,
+                          const Layout &L) override { return small_ragged_t(d, count, base, L); }
+  fst_status small_ragged(const RaggedDesc<double> *d, int count, const ConvArgs<double> &base,
+                          const Layout &L) override { return small_ragged_t(d, count, base, L); }
   fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
   fst_status passA(const ConvArgs<float> &a, const Layout &L) override {
@@ -485,6 +544,26 @@ struct DevRunner : Runner {
   fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
     k_finalize<<<nt, 256, 0, s>>>(x, n, nt, parity, N, S);
     LAUNCHED("k_finalize");
+    return FST_OK;
+  }
+  fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
+                         int *flag) override {
+    k_bisect_many<<<(nt + 127) / 128, 128, 0, s>>>(td, nt, dcat, e2cat, theta, flag);
+    LAUNCHED("k_bisect_many");
+    ++g_launches;
+    return FST_OK;
+  }
+  fst_status invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat, const double *theta,
+                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
+    k_invit_many<<<(nt + 63) / 64, 64, 0, s>>>(td, nt, dcat, ecat, theta, x, fd, fdl, fdu, fdu2, piv);
+    LAUNCHED("k_invit_many");
+    ++g_launches;
+    return FST_OK;
+  }
+  fst_status finalize_many(const TargetDesc *td, int nt, const double *x) override {
+    k_finalize_many<<<nt, 256, 0, s>>>(td, x);
+    LAUNCHED("k_finalize_many");
+    ++g_launches;
     return FST_OK;
   }
   fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) override {
@@ -759,5 +838,107 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
   }
   CU(cudaStreamSynchronize(hp.cout), "sync");
   CU(cudaStreamSynchronize(sc), "sync");
+  return FST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fst_project_ragged: the first call with a given (plans, signals) signature runs
+// directly (allocating what it needs), the second records the whole batch into a
+// CUDA graph, later ones replay it.
+// ---------------------------------------------------------------------------
+namespace {
+struct RaggedCtx {
+  std::vector<const void *> sig;
+  std::vector<void *> bufs;
+  fst::Runner *R = nullptr;   // runner that owns bufs
+  cudaGraphExec_t exec = nullptr;
+  long long nodes = 0;
+  int seen = 0;
+};
+std::mutex g_ragged_mu;
+std::vector<RaggedCtx *> g_ragged;
+cudaStream_t g_ragged_cap = nullptr;
+bool ragged_graphs_enabled() {
+  const char *s = getenv("FST_GRAPHS");
+  return !(s && s[0] == '0');
+}
+}  // namespace
+
+extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *const *y, void *const *out,
+                                         int64_t count, int dtype, void *stream) {
+  if (count < 0 || (count > 0 && (!plans || !y || !out))) return fail(FST_EINVAL, "bad arguments");
+  if (count == 0) return FST_OK;
+  for (int64_t i = 0; i < count; ++i)
+    if (!plans[i]) return fail(FST_EINVAL, "NULL plan");
+  if (!plans[0]->R->device()) {
+    std::vector<void *> bufs;
+    fst_status st = run_ragged(plans, y, out, count, dtype, bufs);
+    for (void *b : bufs) plans[0]->R->release(b);
+    return st;
+  }
+  std::lock_guard<std::mutex> lk(g_ragged_mu);
+  std::vector<const void *> sig;
+  sig.reserve(3 * count + 1);
+  sig.push_back((const void *)(intptr_t)dtype);
+  for (int64_t i = 0; i < count; ++i) {
+    sig.push_back(plans[i]);
+    sig.push_back(y[i]);
+    sig.push_back(out[i]);
+  }
+  RaggedCtx *ctx = nullptr;
+  for (RaggedCtx *c : g_ragged)
+    if (c->sig == sig) ctx = c;
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(us, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;
+  }
+  const bool graphs = ragged_graphs_enabled() && !profiling_enabled() && cs == cudaStreamCaptureStatusNone;
+  if (ctx && ctx->exec && graphs) {
+    CU(cudaGraphLaunch(ctx->exec, us), "cudaGraphLaunch");
+    g_launches += ctx->nodes;
+    return FST_OK;
+  }
+  if (!ctx) {
+    if (g_ragged.size() >= 4) {
+      RaggedCtx *old = g_ragged.front();
+      cudaStreamSynchronize(us);
+      if (old->exec) cudaGraphExecDestroy(old->exec);
+      for (void *b : old->bufs) old->R->release(b);
+      delete old;
+      g_ragged.erase(g_ragged.begin());
+    }
+    ctx = new RaggedCtx();
+    ctx->sig = sig;
+    ctx->R = plans[0]->R;
+    g_ragged.push_back(ctx);
+  }
+  for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream(stream);
+  if (ctx->seen == 0 || !graphs) {
+    ctx->seen = 1;
+    return run_ragged(plans, y, out, count, dtype, ctx->bufs);
+  }
+  // second call: record the batch into a graph on a private stream
+  if (!g_ragged_cap) CU(cudaStreamCreateWithFlags(&g_ragged_cap, cudaStreamNonBlocking), "stream");
+  for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream((void *)g_ragged_cap);
+  const long long l0 = g_launches;
+  CU(cudaStreamBeginCapture(g_ragged_cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  fst_status st = run_ragged(plans, y, out, count, dtype, ctx->bufs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g_ragged_cap, &g);
+  for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream(stream);
+  ctx->nodes = g_launches - l0;
+  g_launches = l0;
+  if (st != FST_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&ctx->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  CU(cudaGraphLaunch(ctx->exec, us), "cudaGraphLaunch");
+  g_launches += ctx->nodes;
   return FST_OK;
 }

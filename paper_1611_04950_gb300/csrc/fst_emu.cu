@@ -92,6 +92,33 @@ struct EmuRunner : Runner {
       }
     return FST_OK;
   }
+  template <typename T>
+  fst_status small_ragged_t(const RaggedDesc<T> *d, int count, const ConvArgs<T> &base, const Layout &L) {
+    std::vector<unsigned char> smem(L.smem_small + 64);
+    const int Lsz = 1 << base.log2M;
+    c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
+    T *red = reinterpret_cast<T *>(smem.data() + padded_size(Lsz) * sizeof(c2<T>));
+    T *coef = red + ((L.nthr_small + 31) / 32) * 128;
+    for (int i = 0; i < count; ++i) {
+      ConvArgs<T> a = base;
+      a.y = d[i].y;
+      a.out = d[i].out;
+      a.ld = d[i].N;
+      a.N = d[i].N;
+      a.spec = d[i].spec;
+      a.ST = d[i].ST;
+      a.D = d[i].D;
+      a.r = d[i].r;
+      a.rpad = d[i].rpad;
+      HostEx<KState<T>> ex(L.nthr_small);
+      small_body<T>(ex, a, 0, buf, red, coef);
+    }
+    return FST_OK;
+  }
+  fst_status small_ragged(const RaggedDesc<float> *d, int count, const ConvArgs<float> &base,
+                          const Layout &L) override { return small_ragged_t(d, count, base, L); }
+  fst_status small_ragged(const RaggedDesc<double> *d, int count, const ConvArgs<double> &base,
+                          const Layout &L) override { return small_ragged_t(d, count, base, L); }
   fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
   fst_status passA(const ConvArgs<float> &a, const Layout &L) override { return passA_t(a, L); }
@@ -122,6 +149,32 @@ struct EmuRunner : Runner {
     for (int t = 0; t < nt; ++t) {
       HostEx<NoStateH> ex(256);
       finalize_body(ex, x, n, nt, t, parity, N, S + (int64_t)t * N, sh.data());
+    }
+    return FST_OK;
+  }
+  fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
+                         int *flag) override {
+    for (int t = 0; t < nt; ++t) {
+      const TargetDesc &q = td[t];
+      bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag);
+    }
+    return FST_OK;
+  }
+  fst_status invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat, const double *theta,
+                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
+    for (int t = 0; t < nt; ++t) {
+      const TargetDesc &q = td[t];
+      invit_body(dcat + q.mat_off, ecat + q.mat_off, q.n, theta[t], q.tol, 3, 0, 1, x + q.x_off, fd + q.x_off,
+                 fdl + q.x_off, fdu + q.x_off, fdu2 + q.x_off, piv + q.x_off);
+    }
+    return FST_OK;
+  }
+  fst_status finalize_many(const TargetDesc *td, int nt, const double *x) override {
+    std::vector<double> sh(2 * 256);
+    for (int t = 0; t < nt; ++t) {
+      const TargetDesc &q = td[t];
+      HostEx<NoStateH> ex(256);
+      finalize_body(ex, x + q.x_off, q.n, 1, 0, q.parity, q.N, q.S, sh.data());
     }
     return FST_OK;
   }

@@ -227,11 +227,15 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   const size_t extra = (L0.split_corr && full && p->r > 0) ? split_corr_bytes(p->N, npairs, (int)p->rpad) : 0;
   if (!ext_ws) {
     Runner *R = p->R;
-    const size_t slot = ws_need(L0, dbl, (int)p->rpad, false);
+    // launch groups no larger than the call needs (small batches, ragged signals)
+    Layout L1 = L0;
+    if (!L1.small) L1.chunk = std::min<int64_t>(L0.chunk, (npairs + L0.G - 1) / L0.G * L0.G);
+    const Layout &Lc = L1;
+    const size_t slot = ws_need(Lc, dbl, (int)p->rpad, false);
     const bool graphs = R->device() && graphs_enabled() && !profiling_enabled() && !R->user_stream_capturing();
     if (!graphs) {
       TRY(ensure_ws(p, slot + extra));
-      return run_conv<T>(R, L0, a, npairs, p->ws);
+      return run_conv<T>(R, Lc, a, npairs, p->ws);
     }
     // whole apply as one cached CUDA graph (two overlapping lanes of launch groups)
     for (auto &e : p->graphs)
@@ -240,9 +244,9 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
         return R->graph_launch(e.exec, e.nodes);
     TRY(ensure_ws(p, 2 * slot + 256 + extra));
     if (!R->graph_begin()) {
-      return run_conv<T>(R, L0, a, npairs, p->ws);
+      return run_conv<T>(R, Lc, a, npairs, p->ws);
     }
-    fst_status st = run_conv<T>(R, L0, a, npairs, p->ws);
+    fst_status st = run_conv<T>(R, Lc, a, npairs, p->ws);
     void *exec = nullptr;
     long long nodes = 0;
     fst_status st2 = R->graph_end(&exec, &nodes);
@@ -394,6 +398,43 @@ static double D_of(double lam, int64_t l, int64_t K, int op, double alpha) {
   return lam / (lam * lam + alpha) - lam / (1.0 + alpha);                      // U5 U5^*, Corollary 4
 }
 
+// lambda_l = s_l^T (B s_l) for the nwin window vectors (rows of S), FP64 convolution
+// with the unit-scaled spectrum
+static fst_status window_eigenvalues(fst_plan_t p, double *S, int nwin, double *lam_host, const double *spec_unit) {
+  Runner *R = p->R;
+  const int64_t N = p->N;
+  Scoped sc(R);
+  double *BS, *lamd;
+  TRY(sc.alloc(&BS, (size_t)nwin * N));
+  TRY(sc.alloc(&lamd, nwin));
+  {
+    ConvArgs<double> a{};
+    a.y = S;
+    a.out = BS;
+    a.ld = N;
+    a.batch = nwin;
+    a.cplx = 0;
+    a.N = N;
+    a.spec = spec_unit;
+    a.r = 0;
+    a.rpad = 0;
+    a.tw = plan_tw<double>(p);
+    a.mode = MODE_CONV;
+    const Layout L = make_layout(N, p->log2M, true, 0);
+    void *ws = nullptr;
+    const size_t need = ws_need(L, true, 0, false);
+    if (need) {
+      char *w;
+      TRY(sc.alloc(&w, need));
+      ws = w;
+    }
+    TRY(run_conv<double>(R, L, a, (nwin + 1) / 2, ws));
+  }
+  TRY(R->dot(S, BS, N, nwin, lamd));
+  TRY(R->d2h(lam_host, lamd, nwin * sizeof(double)));
+  return FST_OK;
+}
+
 // Slepian vectors s^(l), lo <= l <= hi, as rows S[l - lo][0..N), and their
 // eigenvalues lambda_l = s^T B s (FP64 FFT convolution with spec64 = DFT_M(c)/M).
 static fst_status window_vectors(fst_plan_t p, Scoped &sc, int64_t lo, int64_t hi, double *S, double *lam_host,
@@ -456,41 +497,11 @@ static fst_status window_vectors(fst_plan_t p, Scoped &sc, int64_t lo, int64_t h
     for (int k = 0; k < nt; ++k)
       TRY(R->d2d(S + (size_t)(ls[k] - lo) * N, Sp + (size_t)k * N, (size_t)N * sizeof(double)));
   }
-  // lambda_l = s_l^T (B s_l)
-  double *BS, *lamd;
-  TRY(sc.alloc(&BS, (size_t)nwin * N));
-  TRY(sc.alloc(&lamd, nwin));
-  {
-    ConvArgs<double> a{};
-    a.y = S;
-    a.out = BS;
-    a.ld = N;
-    a.batch = nwin;
-    a.cplx = 0;
-    a.N = N;
-    a.spec = spec_unit;
-    a.r = 0;
-    a.rpad = 0;
-    a.tw = plan_tw<double>(p);
-    a.mode = MODE_CONV;
-    const Layout L = make_layout(N, p->log2M, true, 0);
-    Scoped wsc(R);
-    void *ws = nullptr;
-    const size_t need = ws_need(L, true, 0, false);
-    if (need) {
-      char *w;
-      TRY(wsc.alloc(&w, need));
-      ws = w;
-    }
-    TRY(run_conv<double>(R, L, a, (nwin + 1) / 2, ws));
-  }
-  TRY(R->dot(S, BS, N, nwin, lamd));
-  TRY(R->d2h(lam_host, lamd, nwin * sizeof(double)));
-  return FST_OK;
+  return window_eigenvalues(p, S, nwin, lam_host, spec_unit);
 }
 
-fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
-                      double alpha) {
+static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                             double alpha) {
   if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
   *out = nullptr;
   if (!(N >= 1 && N <= (1LL << 23))) { delete R; return fail(FST_EINVAL, "need 1 <= N <= 2^23"); }
@@ -540,6 +551,7 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
   }
 
   Scoped sc(R);
+  sc.ptrs.clear();
   const Layout L64 = make_layout(N, p->log2M, true, 0);
   const Layout L32 = make_layout(N, p->log2M, false, 0);
 
@@ -550,7 +562,8 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     fst_status s;
     if ((s = sc.alloc(&cvec, (size_t)M)) != FST_OK) return bail(s);
     if ((s = sc.alloc(&X, (size_t)M)) != FST_OK) return bail(s);
-    if ((s = sc.alloc(&spec_unit, (size_t)M)) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&spec_unit, (size_t)M * sizeof(double))) != FST_OK) return bail(s);
+    p->spec_unit = spec_unit;
     if ((s = R->alloc((void **)&p->spec64, (size_t)M * sizeof(double))) != FST_OK) return bail(s);
     if ((s = R->alloc((void **)&p->spec32, (size_t)M * sizeof(float))) != FST_OK) return bail(s);
     if ((s = R->sinc_embed(cvec, N, M, W)) != FST_OK) return bail(s);
@@ -590,35 +603,17 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     if ((s = R->spec_store(X, L64, L32, M, p->beta / (double)M, p->spec64, p->spec32)) != FST_OK) return bail(s);
   }
 
-  // eigen-window around the centre, widened until both edges are outside T
-  const int64_t centre = (op == FST_OP_TIKHONOV) ? Kdef : K;
-  int64_t Rw = (int64_t)std::min(ceil(cor1_bound(N, eps)), ceil(0.6 * asymptotic_transition(N, eps)) + 6.0);
-  Rw = std::max<int64_t>(Rw, 2);
-  std::vector<double> lamw;
-  double *S = nullptr;
-  int64_t lo = 0, hi = 0;
-  for (int attempt = 0;; ++attempt) {
-    lo = std::max<int64_t>(0, centre - Rw);
-    hi = std::min<int64_t>(N - 1, centre + Rw);
-    const int nwin = (int)(hi - lo + 1);
-    Scoped win(R);
-    double *Sw;
-    fst_status s;
-    if ((s = win.alloc(&Sw, (size_t)nwin * N)) != FST_OK) return bail(s);
-    lamw.assign(nwin, 0.0);
-    if ((s = window_vectors(p, win, lo, hi, Sw, lamw.data(), spec_unit)) != FST_OK) return bail(s);
-    const bool lo_ok = (lo == 0) || !in_T(lamw[0], lo, K, eps, op, p->alpha);
-    const bool hi_ok = (hi == N - 1) || !in_T(lamw[nwin - 1], hi, K, eps, op, p->alpha);
-    if (lo_ok && hi_ok) {
-      // keep the window's vectors: move ownership of Sw to sc
-      win.ptrs.erase(std::find(win.ptrs.begin(), win.ptrs.end(), (void *)Sw));
-      sc.ptrs.push_back(Sw);
-      S = Sw;
-      break;
-    }
-    if (attempt > 12) return bail(fail(FST_ENOCONVERGE, "eigen-window search did not terminate"));
-    Rw *= 2;
-  }
+  *out = p;
+  return FST_OK;
+}
+
+static fst_status plan_end(fst_plan_t p, double *S, const std::vector<double> &lamw, int64_t lo, int64_t hi) {
+  Runner *R = p->R;
+  const int64_t N = p->N, K = p->K;
+  const double eps = p->eps;
+  const int op = p->op;
+  auto bail = [&](fst_status s) { return s; };
+  Scoped sc(R);
   p->win_lo = lo;
   p->win_hi = hi;
   p->lam_window = lamw;
@@ -665,11 +660,63 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
   if (p->lay64.small && p->lay64.smem_small > 227 * 1024)
     return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
-  *out = p;
+  if (p->spec_unit) {
+    R->release(p->spec_unit);
+    p->spec_unit = nullptr;
+  }
   return FST_OK;
 }
 
 static void free_coef(fst_plan_t p);
+fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                      double alpha) {
+  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
+  *out = nullptr;
+  fst_plan_t p = nullptr;
+  TRY(plan_begin(R, &p, N, W, K, eps, op, alpha));
+  const int64_t Kdef = (int64_t)floor(2.0 * (double)N * W + 0.5);
+  K = p->K;
+  auto bail = [&](fst_status s) {
+    destroy_plan(p);
+    return s;
+  };
+  const double *spec_unit = p->spec_unit;
+  Scoped sc(R);
+  // eigen-window around the centre, widened until both edges are outside T
+  const int64_t centre = (op == FST_OP_TIKHONOV) ? Kdef : K;
+  int64_t Rw = (int64_t)std::min(ceil(cor1_bound(N, eps)), ceil(0.6 * asymptotic_transition(N, eps)) + 6.0);
+  Rw = std::max<int64_t>(Rw, 2);
+  std::vector<double> lamw;
+  double *S = nullptr;
+  int64_t lo = 0, hi = 0;
+  for (int attempt = 0;; ++attempt) {
+    lo = std::max<int64_t>(0, centre - Rw);
+    hi = std::min<int64_t>(N - 1, centre + Rw);
+    const int nwin = (int)(hi - lo + 1);
+    Scoped win(R);
+    double *Sw;
+    fst_status s;
+    if ((s = win.alloc(&Sw, (size_t)nwin * N)) != FST_OK) return bail(s);
+    lamw.assign(nwin, 0.0);
+    if ((s = window_vectors(p, win, lo, hi, Sw, lamw.data(), spec_unit)) != FST_OK) return bail(s);
+    const bool lo_ok = (lo == 0) || !in_T(lamw[0], lo, K, eps, op, p->alpha);
+    const bool hi_ok = (hi == N - 1) || !in_T(lamw[nwin - 1], hi, K, eps, op, p->alpha);
+    if (lo_ok && hi_ok) {
+      // keep the window's vectors: move ownership of Sw to sc
+      win.ptrs.erase(std::find(win.ptrs.begin(), win.ptrs.end(), (void *)Sw));
+      sc.ptrs.push_back(Sw);
+      S = Sw;
+      break;
+    }
+    if (attempt > 12) return bail(fail(FST_ENOCONVERGE, "eigen-window search did not terminate"));
+    Rw *= 2;
+  }
+  fst_status st = plan_end(p, S, lamw, lo, hi);
+  if (st != FST_OK) return bail(st);
+  *out = p;
+  return FST_OK;
+}
+
 void destroy_plan(fst_plan_t p) {
   if (!p) return;
   if (p->R) free_coef(p);
@@ -678,7 +725,7 @@ void destroy_plan(fst_plan_t p) {
     R->sync();
     for (auto &e : p->graphs) R->graph_destroy(e.exec);
     p->graphs.clear();
-    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hi, p->ST32_lo,
+    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hi, p->ST32_lo, p->spec_unit,
                     p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);
@@ -1141,3 +1188,280 @@ fst_status fst_adi_shifts(int64_t N, int r, double *out) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Many plans at once (ragged batches): the eigen stage of every plan's window
+// runs as one batch of independent targets (bisection and inverse iteration one
+// thread per target), the rest per plan.
+// ===========================================================================
+namespace fst {
+
+struct PendingWin {
+  fst_plan_t p;
+  int64_t centre, Rw, lo, hi;
+  double *S;
+  bool done;
+};
+
+static fst_status batched_window_vectors(std::vector<PendingWin *> &grp) {
+  if (grp.empty()) return FST_OK;
+  Runner *R0 = grp[0]->p->R;
+  Scoped sc(R0);
+  // concatenated reduced matrices and one descriptor per target
+  std::vector<double> dcat, ecat, e2cat;
+  std::vector<TargetDesc> td;
+  for (PendingWin *pw : grp) {
+    fst_plan_t p = pw->p;
+    for (int parity = 0; parity < 2; ++parity) {
+      Reduced red = reduced_tridiagonal(p->N, p->W, parity);
+      if (red.n == 0) continue;
+      double glo = 1e300, ghi = -1e300, tnorm = 0.0, emax2 = 0.0;
+      for (int i = 0; i < red.n; ++i) {
+        const double el = fabs(red.e[i]), er = (i + 1 < red.n) ? fabs(red.e[i + 1]) : 0.0;
+        glo = std::min(glo, red.d[i] - el - er);
+        ghi = std::max(ghi, red.d[i] + el + er);
+        tnorm = std::max(tnorm, fabs(red.d[i]) + el + er);
+        emax2 = std::max(emax2, red.e2[i]);
+      }
+      const double pivmin = 2.2250738585072014e-308 * std::max(1.0, emax2);
+      const double widen = 2.220446049250313e-16 * tnorm * 4.0 + 4.0 * pivmin;
+      const int64_t off = (int64_t)dcat.size();
+      dcat.insert(dcat.end(), red.d.begin(), red.d.end());
+      ecat.insert(ecat.end(), red.e.begin(), red.e.end());
+      e2cat.insert(e2cat.end(), red.e2.begin(), red.e2.end());
+      for (int64_t l = pw->lo; l <= pw->hi; ++l) {
+        if ((l & 1) != parity) continue;
+        TargetDesc q{};
+        q.mat_off = off;
+        q.x_off = 0;
+        q.S = pw->S + (size_t)(l - pw->lo) * p->N;
+        q.N = p->N;
+        q.n = red.n;
+        q.target = red.n - 1 - (int)(l >> 1);
+        q.parity = parity;
+        q.glo = glo - widen;
+        q.ghi = ghi + widen;
+        q.pivmin = pivmin;
+        q.tol = 2.220446049250313e-16 * tnorm;
+        td.push_back(q);
+      }
+    }
+  }
+  const int nt = (int)td.size();
+  double *dd, *de, *de2, *theta;
+  int *flag;
+  TargetDesc *dtd;
+  TRY(sc.alloc(&dd, dcat.size()));
+  TRY(sc.alloc(&de, ecat.size()));
+  TRY(sc.alloc(&de2, e2cat.size()));
+  TRY(sc.alloc(&theta, nt));
+  TRY(sc.alloc(&flag, 1));
+  TRY(sc.alloc(&dtd, nt));
+  TRY(R0->h2d(dd, dcat.data(), dcat.size() * sizeof(double)));
+  TRY(R0->h2d(de, ecat.data(), ecat.size() * sizeof(double)));
+  TRY(R0->h2d(de2, e2cat.data(), e2cat.size() * sizeof(double)));
+  TRY(R0->zero(flag, sizeof(int)));
+  TRY(R0->h2d(dtd, td.data(), td.size() * sizeof(TargetDesc)));
+  TRY(R0->bisect_many(dtd, nt, dd, de2, theta, flag));
+  int hflag = 0;
+  TRY(R0->d2h(&hflag, flag, sizeof(int)));
+  if (hflag) return fail(FST_ENOCONVERGE, "bisection did not converge");
+  // inverse iteration and expansion in groups bounded by the factor storage
+  const int64_t budget = 48LL << 20;   // elements per factor array
+  for (int t0 = 0; t0 < nt;) {
+    int t1 = t0;
+    int64_t tot = 0;
+    while (t1 < nt && (tot + td[t1].n <= budget || t1 == t0)) {
+      td[t1].x_off = tot;
+      tot += td[t1].n;
+      ++t1;
+    }
+    Scoped g(R0);
+    double *x, *fd, *fdl, *fdu, *fdu2;
+    uint8_t *piv;
+    TargetDesc *gtd;
+    TRY(g.alloc(&x, tot));
+    TRY(g.alloc(&fd, tot));
+    TRY(g.alloc(&fdl, tot));
+    TRY(g.alloc(&fdu, tot));
+    TRY(g.alloc(&fdu2, tot));
+    TRY(g.alloc(&piv, tot));
+    TRY(g.alloc(&gtd, t1 - t0));
+    TRY(R0->h2d(gtd, td.data() + t0, (size_t)(t1 - t0) * sizeof(TargetDesc)));
+    TRY(R0->invit_many(gtd, t1 - t0, dd, de, theta + t0, x, fd, fdl, fdu, fdu2, piv));
+    TRY(R0->finalize_many(gtd, t1 - t0, x));
+    TRY(R0->sync());
+    t0 = t1;
+  }
+  return FST_OK;
+}
+
+fst_status build_plans_many(Runner *(*mk)(), void *stream, int64_t count, const int64_t *N, const double *W,
+                            const int64_t *K, const double *eps, fst_plan_t *out) {
+  if (!out || count < 0 || (count > 0 && (!N || !W || !eps))) return fail(FST_EINVAL, "bad arguments");
+  for (int64_t i = 0; i < count; ++i) out[i] = nullptr;
+  auto cleanup = [&](fst_status s) {
+    for (int64_t i = 0; i < count; ++i) {
+      destroy_plan(out[i]);
+      out[i] = nullptr;
+    }
+    return s;
+  };
+  std::vector<PendingWin> pw(count);
+  for (int64_t i = 0; i < count; ++i) {
+    Runner *R = mk();
+    if (!R) return cleanup(fail(FST_ECUDA, "no CUDA device"));
+    R->set_stream(stream);
+    fst_status s = plan_begin(R, &out[i], N[i], W[i], K ? K[i] : -1, eps[i], FST_OP_PROJECT, 0.0);
+    if (s != FST_OK) return cleanup(s);
+    fst_plan_t p = out[i];
+    pw[i].p = p;
+    pw[i].centre = p->K;
+    pw[i].Rw = std::max<int64_t>(
+        2, (int64_t)std::min(ceil(cor1_bound(p->N, p->eps)), ceil(0.6 * asymptotic_transition(p->N, p->eps)) + 6.0));
+    pw[i].S = nullptr;
+    pw[i].done = false;
+  }
+  for (int attempt = 0; attempt < 14; ++attempt) {
+    std::vector<PendingWin *> pend;
+    for (auto &q : pw)
+      if (!q.done) pend.push_back(&q);
+    if (pend.empty()) break;
+    // groups bounded by the host/device size of the window vectors
+    size_t gi = 0;
+    while (gi < pend.size()) {
+      std::vector<PendingWin *> grp;
+      int64_t elems = 0;
+      while (gi < pend.size() && (grp.empty() || elems < (256LL << 20))) {
+        PendingWin *q = pend[gi++];
+        fst_plan_t p = q->p;
+        q->lo = std::max<int64_t>(0, q->centre - q->Rw);
+        q->hi = std::min<int64_t>(p->N - 1, q->centre + q->Rw);
+        const int64_t nwin = q->hi - q->lo + 1;
+        fst_status s = p->R->alloc((void **)&q->S, (size_t)nwin * p->N * sizeof(double));
+        if (s != FST_OK) return cleanup(s);
+        elems += nwin * p->N;
+        grp.push_back(q);
+      }
+      fst_status s = batched_window_vectors(grp);
+      if (s != FST_OK) return cleanup(s);
+      for (PendingWin *q : grp) {
+        fst_plan_t p = q->p;
+        const int nwin = (int)(q->hi - q->lo + 1);
+        std::vector<double> lamw(nwin);
+        s = window_eigenvalues(p, q->S, nwin, lamw.data(), p->spec_unit);
+        if (s != FST_OK) return cleanup(s);
+        const bool lo_ok = (q->lo == 0) || !in_T(lamw[0], q->lo, p->K, p->eps, p->op, p->alpha);
+        const bool hi_ok = (q->hi == p->N - 1) || !in_T(lamw[nwin - 1], q->hi, p->K, p->eps, p->op, p->alpha);
+        if (lo_ok && hi_ok) {
+          s = plan_end(p, q->S, lamw, q->lo, q->hi);
+          q->done = true;
+        } else {
+          q->Rw *= 2;
+        }
+        p->R->release(q->S);
+        q->S = nullptr;
+        if (s != FST_OK) return cleanup(s);
+      }
+    }
+  }
+  for (auto &q : pw)
+    if (!q.done) return cleanup(fail(FST_ENOCONVERGE, "eigen-window search did not terminate"));
+  return FST_OK;
+}
+
+}  // namespace fst
+
+extern "C" {
+
+fst_status fst_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const double *W, const int64_t *K,
+                         const double *eps, void *stream) {
+  return build_plans_many(make_dev_runner, stream, count, N, W, K, eps, out);
+}
+
+fst_status fst_emu_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const double *W, const int64_t *K,
+                             const double *eps) {
+  return build_plans_many(make_emu_runner, nullptr, count, N, W, K, eps, out);
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Ragged batches: signal i with its own plan plans[i]
+// ===========================================================================
+namespace fst {
+
+template <typename T>
+static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count,
+                           bool cplx, std::vector<void *> &desc_bufs) {
+  const bool dbl = sizeof(T) == 8;
+  // single-CTA signals by FFT length, one launch each
+  std::vector<std::vector<RaggedDesc<T>>> buckets(32);
+  std::vector<int> maxr(32, 0);
+  std::vector<int64_t> others;
+  size_t reuse = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    fst_plan_t p = plans[i];
+    const Layout &L = dbl ? p->lay64 : p->lay32;
+    if (L.small) {
+      RaggedDesc<T> d;
+      d.y = (const T *)y[i];
+      d.out = (T *)out[i];
+      d.spec = (const T *)(dbl ? (const void *)p->spec64 : (const void *)p->spec32);
+      d.ST = (const T *)(dbl ? (const void *)p->ST64 : (const void *)p->ST32);
+      d.D = (const T *)(dbl ? (const void *)p->D64 : (const void *)p->D32);
+      d.N = p->N;
+      d.r = (int)p->r;
+      d.rpad = (int)p->rpad;
+      buckets[p->log2M].push_back(d);
+      maxr[p->log2M] = std::max(maxr[p->log2M], (int)p->rpad);
+    } else {
+      others.push_back(i);
+    }
+  }
+  for (int lg = 0; lg < 32; ++lg) {
+    if (buckets[lg].empty()) continue;
+    fst_plan_t p0 = nullptr;
+    for (int64_t i = 0; i < count && !p0; ++i)
+      if (plans[i]->log2M == lg && (dbl ? plans[i]->lay64 : plans[i]->lay32).small) p0 = plans[i];
+    Runner *R = p0->R;
+    Layout L = make_layout(p0->N, lg, dbl, maxr[lg], false);
+    void *dd = nullptr;
+    if (reuse < desc_bufs.size()) {
+      dd = desc_bufs[reuse++];   // same signature as the call that filled it
+    } else {
+      TRY(R->alloc(&dd, buckets[lg].size() * sizeof(RaggedDesc<T>)));
+      desc_bufs.push_back(dd);
+      reuse = desc_bufs.size();
+      TRY(R->h2d(dd, buckets[lg].data(), buckets[lg].size() * sizeof(RaggedDesc<T>)));
+    }
+    ConvArgs<T> base{};
+    base.batch = 1;
+    base.cplx = cplx ? 1 : 0;
+    base.log2M = lg;
+    base.tw = plan_tw<T>(p0);
+    base.mode = MODE_FULL;
+    base.pair0 = 0;
+    base.npairs = 1;
+    TRY(R->small_ragged((const RaggedDesc<T> *)dd, (int)buckets[lg].size(), base, L));
+  }
+  for (int64_t i : others) TRY(run_apply(plans[i], y[i], out[i], 1, 0, cplx ? (dbl ? FST_C128 : FST_C64) : (dbl ? FST_F64 : FST_F32), true));
+  return FST_OK;
+}
+
+fst_status run_ragged(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count, int dtype,
+                      std::vector<void *> &desc_bufs) {
+  if (count < 0 || (count > 0 && (!plans || !y || !out))) return fail(FST_EINVAL, "bad arguments");
+  for (int64_t i = 0; i < count; ++i)
+    if (!plans[i] || !y[i] || !out[i]) return fail(FST_EINVAL, "NULL plan or signal pointer");
+  if (count == 0) return FST_OK;
+  switch (dtype) {
+    case FST_F32: return ragged_t<float>(plans, y, out, count, false, desc_bufs);
+    case FST_C64: return ragged_t<float>(plans, y, out, count, true, desc_bufs);
+    case FST_F64: return ragged_t<double>(plans, y, out, count, false, desc_bufs);
+    case FST_C128: return ragged_t<double>(plans, y, out, count, true, desc_bufs);
+    default: return fail(FST_EINVAL, "unknown dtype");
+  }
+}
+
+}  // namespace fst

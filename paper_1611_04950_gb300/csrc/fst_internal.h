@@ -53,6 +53,11 @@ struct Runner {
   virtual fst_status passB(const ConvArgs<double> &a, const Layout &L) = 0;
   virtual fst_status passC(const ConvArgs<float> &a, const Layout &L) = 0;
   virtual fst_status passC(const ConvArgs<double> &a, const Layout &L) = 0;
+  // ragged batch: one single-CTA transform per descriptor (all with FFT length 2^base.log2M)
+  virtual fst_status small_ragged(const RaggedDesc<float> *d, int count, const ConvArgs<float> &base,
+                                  const Layout &L) = 0;
+  virtual fst_status small_ragged(const RaggedDesc<double> *d, int count, const ConvArgs<double> &base,
+                                  const Layout &L) = 0;
   // separate correction (FP32, device): partials, reduce to a = D o c, out += S_T a
   virtual fst_status corr_c(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
   virtual fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) { return FST_EUNSUPPORTED; }
@@ -65,6 +70,13 @@ struct Runner {
                            int iters, double *x, double *fd, double *fdl, double *fdu, double *fdu2,
                            uint8_t *piv) = 0;
   virtual fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) = 0;
+  // batched eigen-targets of many plans (descriptors and data in runner memory)
+  virtual fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat,
+                                 double *theta, int *flag) = 0;
+  virtual fst_status invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat,
+                                const double *theta, double *x, double *fd, double *fdl, double *fdu, double *fdu2,
+                                uint8_t *piv) = 0;
+  virtual fst_status finalize_many(const TargetDesc *td, int nt, const double *x) = 0;
   virtual fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) = 0;
   virtual fst_status sinc_embed(double *c, int64_t N, int64_t M, double W) = 0;
   virtual fst_status spec_store(const double2 *X, const Layout &L64, const Layout &L32, int64_t M, double scale,
@@ -120,6 +132,7 @@ struct fst_plan_s {
   fst::Layout lay32, lay64;
   float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr, *ST32_hi = nullptr, *ST32_lo = nullptr;
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
+  double *spec_unit = nullptr;   // plan-time only: DFT_M(c) / M for the eigenvalues
   float2 *tw32h = nullptr, *tw32l = nullptr;
   double2 *tw64h = nullptr, *tw64l = nullptr;
   void *ws = nullptr;
@@ -153,4 +166,10 @@ fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, i
                         void *ws, size_t ws_bytes);
 void destroy_plan(fst_plan_t p);
 bool profiling_enabled();   // per-launch event timing is on (fst_profile_enable)
+// ragged batch on the plans' runners; descriptor buffers it allocates are appended
+// to desc_bufs (the caller owns them); buffers already in desc_bufs are reused
+fst_status run_ragged(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count, int dtype,
+                      std::vector<void *> &desc_bufs);
+fst_status build_plans_many(Runner *(*mk)(), void *stream, int64_t count, const int64_t *N, const double *W,
+                            const int64_t *K, const double *eps, fst_plan_t *out);
 }  // namespace fst

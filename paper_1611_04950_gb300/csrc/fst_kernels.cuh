@@ -99,6 +99,17 @@ FST_HD float tf32_round(float x) {
   return v.f;
 }
 
+// One signal of a ragged batch processed by the single-CTA kernel (its own plan).
+template <typename T> struct RaggedDesc {
+  const T *y;
+  T *out;
+  const T *spec;
+  const T *ST;
+  const T *D;
+  int64_t N;
+  int r, rpad;
+};
+
 template <typename T> struct KState {
   c2<T> v[16];
 };

@@ -84,6 +84,35 @@ FST_HD void bisect_body(Ex &ex, const double *d, const double *e2, int n, int ta
   });
 }
 
+// Plain bisection for one target (one thread), used when many plans are built at
+// once: the throughput of thousands of independent targets matters more than the
+// latency of one.  flag != 0 if it did not converge.
+FST_HD void bisect1_body(const double *d, const double *e2, int n, int target, double glo, double ghi, double pivmin,
+                         double *out, int *flag) {
+  double lo = glo, hi = ghi;
+  int it = 0;
+  for (; it < 256; ++it) {
+    const double tol = 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
+    if (hi - lo <= tol) break;
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e2, n, mid, pivmin) > target) hi = mid;
+    else lo = mid;
+  }
+  *out = 0.5 * (lo + hi);
+  if (it == 256) *flag = 1;
+}
+
+// Descriptor of one eigen-target of a batch of plans (fst_plan_many).
+struct TargetDesc {
+  int64_t mat_off;   // reduced matrix: d, e, e2 at [mat_off, mat_off + n) of the concatenations
+  int64_t x_off;     // this target's vector and factor arrays at [x_off, x_off + n)
+  double *S;         // output: the full unit-norm Slepian vector (length N)
+  int64_t N;
+  int n, target, parity, pad_;
+  double glo, ghi, pivmin, tol;
+};
+
 // Inverse iteration for one eigenvalue sigma of the reduced matrix (diag d,
 // coupling e[i] between i-1 and i): LU with partial pivoting of T - sigma I (the
 // classical tridiagonal elimination; row interchanges create a second

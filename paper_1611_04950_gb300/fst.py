@@ -34,7 +34,7 @@ EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_
             "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
             "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
             "fst_project_noalloc", "fst_noalloc_scratch_bytes", "fst_coeffs", "fst_coeffs_info",
-            "fst_adi_shifts"]
+            "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged"]
 
 
 class FSTError(RuntimeError):
@@ -67,6 +67,9 @@ def _load():
         "fst_coeffs": ([P, vp, vp, i64, i64, I, vp], I),
         "fst_coeffs_info": ([P] + [C.POINTER(i64)] * 6, I),
         "fst_adi_shifts": ([i64, I, C.POINTER(d)], I),
+        "fst_plan_many": ([C.POINTER(P), i64, C.POINTER(i64), C.POINTER(d), C.POINTER(i64), C.POINTER(d), vp], I),
+        "fst_emu_plan_many": ([C.POINTER(P), i64, C.POINTER(i64), C.POINTER(d), C.POINTER(i64), C.POINTER(d)], I),
+        "fst_project_ragged": ([C.POINTER(P), C.POINTER(vp), C.POINTER(vp), i64, I, vp], I),
         "fst_noalloc_scratch_bytes": ([], C.c_ulonglong),
         "fst_profile_enable": ([I], I),
         "fst_profile_count": ([], I),
@@ -176,6 +179,70 @@ def fst_adi_shifts(N: int, r: int) -> np.ndarray:
     out = np.zeros(r)
     _check(_lib.fst_adi_shifts(N, r, out.ctypes.data_as(C.POINTER(C.c_double))))
     return out
+
+
+def fst_plan_many(Ns, Ws, epss, Ks=None, stream=None, emulate: bool = False) -> list:
+    """Handles of len(Ns) projection plans built together (fst_plan_many)."""
+    n = len(Ns)
+    out = (C.c_void_p * n)()
+    Na = (C.c_int64 * n)(*[int(v) for v in Ns])
+    Wa = (C.c_double * n)(*[float(v) for v in Ws])
+    Ea = (C.c_double * n)(*[float(v) for v in epss])
+    Ka = None if Ks is None else (C.c_int64 * n)(*[int(v) for v in Ks])
+    cast = lambda a, t: C.cast(a, C.POINTER(t)) if a is not None else None
+    if emulate:
+        _check(_lib.fst_emu_plan_many(cast(out, C.c_void_p), n, cast(Na, C.c_int64), cast(Wa, C.c_double),
+                                      cast(Ka, C.c_int64), cast(Ea, C.c_double)))
+    else:
+        _check(_lib.fst_plan_many(cast(out, C.c_void_p), n, cast(Na, C.c_int64), cast(Wa, C.c_double),
+                                  cast(Ka, C.c_int64), cast(Ea, C.c_double), C.c_void_p(_stream_handle(stream))))
+    return [out[i] for i in range(n)]
+
+
+def fst_project_ragged(handles, y_ptrs, out_ptrs, dtype: int, stream: int = 0):
+    n = len(handles)
+    Pa = (C.c_void_p * n)(*handles)
+    Ya = (C.c_void_p * n)(*y_ptrs)
+    Oa = (C.c_void_p * n)(*out_ptrs)
+    _check(_lib.fst_project_ragged(C.cast(Pa, C.POINTER(C.c_void_p)), C.cast(Ya, C.POINTER(C.c_void_p)),
+                                   C.cast(Oa, C.POINTER(C.c_void_p)), n, dtype, C.c_void_p(stream)))
+
+
+class PlanSet:
+    """Plans of a ragged batch (one per signal), built with fst_plan_many."""
+
+    def __init__(self, params, stream=None, emulate: bool = False):
+        Ns, Ws, es = zip(*params) if params else ((), (), ())
+        self.params = list(params)
+        self.emulated = emulate
+        self.h = fst_plan_many(Ns, Ws, es, stream=stream, emulate=emulate)
+
+    def close(self):
+        for h in getattr(self, "h", []) or []:
+            fst_destroy(h)
+        self.h = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, i: int) -> dict:
+        return fst_plan_info(self.h[i])
+
+    def project(self, ys, outs=None, stream=None):
+        """ys: list of (N_i,) device tensors (numpy arrays for an emulated set)."""
+        if self.emulated:
+            outs = [np.empty_like(v) for v in ys] if outs is None else outs
+            fst_project_ragged(self.h, [v.ctypes.data for v in ys], [o.ctypes.data for o in outs],
+                               _dtype_code(ys[0].dtype), 0)
+            return outs
+        import torch
+        outs = [torch.empty_like(v) for v in ys] if outs is None else outs
+        fst_project_ragged(self.h, [v.data_ptr() for v in ys], [o.data_ptr() for o in outs],
+                           _dtype_code(ys[0].dtype), _stream_handle(stream))
+        return outs
 
 
 def fst_destroy(h: int):

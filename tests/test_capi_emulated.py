@@ -240,3 +240,28 @@ def test_coeffs_need_power_of_two_and_projection():
     with pytest.raises(F.FSTError) as ei:
         q.coeffs(np.zeros((1, 128)))
     assert ei.value.status == F.FST_EINVAL
+
+
+# ---------------------------------------------------------------- ragged batches
+
+def test_emulated_plan_many_and_ragged_projection():
+    from paper_1611_04950_gb300 import workloads
+    params = workloads.ragged_params(10, seed=3, n_lo=100, n_hi=20000)
+    ps = F.PlanSet(params, emulate=True)
+    rng = np.random.default_rng(0)
+    ys = [rng.standard_normal(N) for (N, W, e) in params]
+    plans = [O.make_plan(N, W, None, e) for (N, W, e) in params]
+    for i, ((N, W, e), op) in enumerate(zip(params, plans)):
+        ex = F.fst_plan_export(ps.h[i], N)
+        assert ps.info(i)["r"] == op.r
+        assert np.array_equal(ex["idx"], op.idx)
+        assert np.max(np.abs(ex["S_T"] - op.S_T)) < 1e-9
+    for dt, tol in ((np.float64, 1e-12), (np.float32, 1e-6)):
+        outs = ps.project([y.astype(dt) for y in ys])
+        for y, o, op in zip(ys, outs, plans):
+            assert np.linalg.norm(o - O.fast_project(op, y)) <= tol * np.linalg.norm(y)
+
+
+def test_plan_many_rejects_bad_arguments():
+    with pytest.raises(F.FSTError):
+        F.fst_plan_many([100, 0], [0.1, 0.1], [1e-6, 1e-6], emulate=True)

@@ -285,3 +285,31 @@ def test_c4m_full_batch_sampled_projection_and_coeffs():
     c = coef[idx].cpu().numpy()
     assert c.shape == ref.shape
     assert np.all(np.abs(c - ref) <= 1e-5 * np.linalg.norm(y, axis=1)[:, None])
+
+
+# ---------------------------------------------------------------- ragged batches
+
+def test_ragged_batch_against_oracle_and_replay():
+    dev = _cuda()
+    params = workloads.ragged_params(48, seed=3)          # N log-uniform in [1000, 262144]
+    ps = F.PlanSet(params)
+    rng = np.random.default_rng(7)
+    ys64 = [rng.standard_normal(N) for (N, W, e) in params]
+    ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in ys64]
+    outs = [torch.empty_like(v) for v in ys]
+    ps.project(ys, outs)                 # direct
+    first = [o.clone() for o in outs]
+    ps.project(ys, outs)                 # recorded into a graph
+    ps.project(ys, outs)                 # replayed
+    torch.cuda.synchronize()
+    for a, b in zip(first, outs):
+        assert torch.equal(a, b)
+    order = np.argsort([N for (N, W, e) in params])
+    check = list(order[:3]) + list(order[len(order) // 2:len(order) // 2 + 2]) + list(order[-2:])
+    for i in check:
+        N, W, e = params[i]
+        op = oplan(N, W, O.default_K(N, W), e)
+        assert ps.info(i)["r"] == op.r
+        ref = O.fast_project(op, ys64[i])
+        err = np.linalg.norm(outs[i].double().cpu().numpy() - ref) / np.linalg.norm(ys64[i])
+        assert err < 1e-5, (i, N, err)
