@@ -234,11 +234,10 @@ __global__ void k_coef_mix(const CoefArgs<T> a, const T *tot, const T *totU, con
       coef_mix_value<T>(a, tot + sig * (int64_t)a.nraw * 2, totU + sig * (int64_t)(a.r > 0 ? a.r : 1) * 2, CA, CB, sq, o, sig);
 }
 
-__global__ void k_split_tf32(const float *src, float *hi, float *lo, int64_t n) {
+__global__ void k_split_tf32(const float *src, float2 *hl, int64_t n) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const float h = tf32_round(src[t]);
-    hi[t] = h;
-    lo[t] = tf32_round(src[t] - h);
+    hl[t] = make_float2(h, tf32_round(src[t] - h));
   }
 }
 
@@ -477,7 +476,7 @@ struct DevRunner : Runner {
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
   fst_status passA(const ConvArgs<float> &a, const Layout &L) override {
     if (!L.fast) return passA_t(a, L);
-    FastArgs f{a, a.ST_hi, a.ST_lo};
+    FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     const int P = 1 << L.log2P;
     if (P == 32) PROF("k_fastA<32>", a.npairs, (k_fastA<32><<<grid, FAST_THREADS, 0, cur>>>(f)));
@@ -498,7 +497,7 @@ struct DevRunner : Runner {
   }
   fst_status passB(const ConvArgs<double> &a, const Layout &L) override { return passB_t(a, L); }
   fst_status corr_c(const ConvArgs<float> &a) override {
-    FastArgs f{a, a.ST_hi, a.ST_lo};
+    FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)((a.N + CORR_BLOCK - 1) / CORR_BLOCK), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     PROF("k_corr_c", a.npairs, (k_corr_c<<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_corr_c");
@@ -510,7 +509,7 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   fst_status corr_z(const ConvArgs<float> &a) override {
-    FastArgs f{a, a.ST_hi, a.ST_lo};
+    FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)((a.N + CORR_ROWS - 1) / CORR_ROWS), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     PROF("k_corr_z", a.npairs, (k_corr_z<<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_corr_z");
@@ -518,7 +517,7 @@ struct DevRunner : Runner {
   }
   fst_status passC(const ConvArgs<float> &a, const Layout &L) override {
     if (!L.fast) return passC_t(a, L);
-    FastArgs f{a, a.ST_hi, a.ST_lo};
+    FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     const int P = 1 << L.log2P;
     if (P == 32) PROF("k_fastC<32>", a.npairs, (k_fastC<32><<<grid, FAST_THREADS, 0, cur>>>(f)));
@@ -651,8 +650,8 @@ struct DevRunner : Runner {
     return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
   }
 
-  fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
-    k_split_tf32<<<grid_for(n, 256), 256, 0, s>>>(src, hi, lo, n);
+  fst_status split_tf32(const float *src, float2 *hl, int64_t n) override {
+    k_split_tf32<<<grid_for(n, 256), 256, 0, s>>>(src, hl, n);
     LAUNCHED("k_split_tf32");
     return FST_OK;
   }

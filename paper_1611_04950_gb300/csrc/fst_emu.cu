@@ -284,10 +284,10 @@ struct EmuRunner : Runner {
     return coef_mix_t(a, tot, totU, CA, CB, sq, out, Kp, nF);
   }
 
-  fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) override {
+  fst_status split_tf32(const float *src, float2 *hl, int64_t n) override {
     for (int64_t i = 0; i < n; ++i) {
-      hi[i] = tf32_round(src[i]);
-      lo[i] = tf32_round(src[i] - hi[i]);
+      const float h = tf32_round(src[i]);
+      hl[i] = make_float2(h, tf32_round(src[i] - h));
     }
     return FST_OK;
   }

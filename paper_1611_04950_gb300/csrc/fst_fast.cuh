@@ -27,8 +27,7 @@ constexpr int YT_STRIDE = 516; // padded row stride (floats) of the signal-major
 
 struct FastArgs {
   ConvArgs<float> a;
-  const float *ST_hi;   // [N][rpad] TF32-rounded S_T
-  const float *ST_lo;   // [N][rpad] TF32(S_T - ST_hi)
+  const float2 *ST_hl;  // [N][rpad] (TF32-rounded S_T, TF32 of the remainder) interleaved
 };
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -176,11 +175,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastA(const FastArgs f) {
           const int jt = jt0 + t;
           if (jt < ntj) {
             const int j = jt * 8 + gid;
-            uint32_t bhi[2], blo[2];
-            bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
-            blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
-            bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
-            blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
+            const float2 sa = okA ? __ldg(f.ST_hl + nA * a.rpad + j) : make_float2(0.f, 0.f);
+            const float2 sb = okB ? __ldg(f.ST_hl + nB * a.rpad + j) : make_float2(0.f, 0.f);
+            const uint32_t bhi[2] = {__float_as_uint(sa.x), __float_as_uint(sb.x)};
+            const uint32_t blo[2] = {__float_as_uint(sa.y), __float_as_uint(sb.y)};
             mma3(acc[t], ahi, alo, bhi, blo);
           }
         }
@@ -360,15 +358,15 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
           const int jt = jt0 + kt;
           if (jt < ntj) {
             const int j0 = jt * 8 + tig, j1 = j0 + 4;
-            uint32_t ahi[4], alo[4];
-            ahi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j0)) : 0u;
-            ahi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j0)) : 0u;
-            ahi[2] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j1)) : 0u;
-            ahi[3] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j1)) : 0u;
-            alo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j0)) : 0u;
-            alo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j0)) : 0u;
-            alo[2] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j1)) : 0u;
-            alo[3] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j1)) : 0u;
+            const float2 z2 = make_float2(0.f, 0.f);
+            const float2 s0 = okA ? __ldg(f.ST_hl + nA * a.rpad + j0) : z2;
+            const float2 s1 = okB ? __ldg(f.ST_hl + nB * a.rpad + j0) : z2;
+            const float2 s2 = okA ? __ldg(f.ST_hl + nA * a.rpad + j1) : z2;
+            const float2 s3 = okB ? __ldg(f.ST_hl + nB * a.rpad + j1) : z2;
+            const uint32_t ahi[4] = {__float_as_uint(s0.x), __float_as_uint(s1.x), __float_as_uint(s2.x),
+                                     __float_as_uint(s3.x)};
+            const uint32_t alo[4] = {__float_as_uint(s0.y), __float_as_uint(s1.y), __float_as_uint(s2.y),
+                                     __float_as_uint(s3.y)};
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               // B (8 j x 8 signals): b0 = A[j = kt*8 + tig][s = u*8 + gid], b1 = A[j + 4][s]
@@ -494,11 +492,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 2) k_corr_c(const FastArgs f) {
           const int jt = jt0 + t;
           if (jt < ntj) {
             const int j = jt * 8 + gid;
-            uint32_t bhi[2], blo[2];
-            bhi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j)) : 0u;
-            blo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j)) : 0u;
-            bhi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j)) : 0u;
-            blo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j)) : 0u;
+            const float2 sa = okA ? __ldg(f.ST_hl + nA * a.rpad + j) : make_float2(0.f, 0.f);
+            const float2 sb = okB ? __ldg(f.ST_hl + nB * a.rpad + j) : make_float2(0.f, 0.f);
+            const uint32_t bhi[2] = {__float_as_uint(sa.x), __float_as_uint(sb.x)};
+            const uint32_t blo[2] = {__float_as_uint(sa.y), __float_as_uint(sb.y)};
             mma3(acc[t], ahi, alo, bhi, blo);
           }
         }
@@ -579,15 +576,15 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_corr_z(const FastArgs f) {
         const int jt = jt0 + kt;
         if (jt < ntj) {
           const int j0 = jt * 8 + tig, j1 = j0 + 4;
-          uint32_t ahi[4], alo[4];
-          ahi[0] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j0)) : 0u;
-          ahi[1] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j0)) : 0u;
-          ahi[2] = okA ? __float_as_uint(__ldg(f.ST_hi + nA * a.rpad + j1)) : 0u;
-          ahi[3] = okB ? __float_as_uint(__ldg(f.ST_hi + nB * a.rpad + j1)) : 0u;
-          alo[0] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j0)) : 0u;
-          alo[1] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j0)) : 0u;
-          alo[2] = okA ? __float_as_uint(__ldg(f.ST_lo + nA * a.rpad + j1)) : 0u;
-          alo[3] = okB ? __float_as_uint(__ldg(f.ST_lo + nB * a.rpad + j1)) : 0u;
+          const float2 z2 = make_float2(0.f, 0.f);
+          const float2 s0 = okA ? __ldg(f.ST_hl + nA * a.rpad + j0) : z2;
+          const float2 s1 = okB ? __ldg(f.ST_hl + nB * a.rpad + j0) : z2;
+          const float2 s2 = okA ? __ldg(f.ST_hl + nA * a.rpad + j1) : z2;
+          const float2 s3 = okB ? __ldg(f.ST_hl + nB * a.rpad + j1) : z2;
+          const uint32_t ahi[4] = {__float_as_uint(s0.x), __float_as_uint(s1.x), __float_as_uint(s2.x),
+                                   __float_as_uint(s3.x)};
+          const uint32_t alo[4] = {__float_as_uint(s0.y), __float_as_uint(s1.y), __float_as_uint(s2.y),
+                                   __float_as_uint(s3.y)};
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             uint32_t bhi[2], blo[2];

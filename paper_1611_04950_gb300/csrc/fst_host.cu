@@ -214,8 +214,7 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.spec = spec;
   a.ST = ST;
   if (sizeof(T) == 4) {
-    a.ST_hi = (const T *)p->ST32_hi;
-    a.ST_lo = (const T *)p->ST32_lo;
+    a.ST_hl = (const c2<T> *)p->ST32_hl;
   }
   a.r = full ? (int)p->r : 0;
   a.rpad = (int)p->rpad;
@@ -649,9 +648,8 @@ static fst_status plan_end(fst_plan_t p, double *S, const std::vector<double> &l
       if ((s = R->zero(p->ST32, nst * sizeof(float))) != FST_OK) return bail(s);
     }
     if ((s = R->to_f32(p->D64, p->D32, p->rpad)) != FST_OK) return bail(s);
-    if ((s = R->alloc((void **)&p->ST32_hi, nst * sizeof(float))) != FST_OK) return bail(s);
-    if ((s = R->alloc((void **)&p->ST32_lo, nst * sizeof(float))) != FST_OK) return bail(s);
-    if ((s = R->split_tf32(p->ST32, p->ST32_hi, p->ST32_lo, (int64_t)nst)) != FST_OK) return bail(s);
+    if ((s = R->alloc((void **)&p->ST32_hl, nst * sizeof(float2))) != FST_OK) return bail(s);
+    if ((s = R->split_tf32(p->ST32, p->ST32_hl, (int64_t)nst)) != FST_OK) return bail(s);
     if ((s = R->sync()) != FST_OK) return bail(s);
   }
   p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad, R->device());
@@ -725,7 +723,7 @@ void destroy_plan(fst_plan_t p) {
     R->sync();
     for (auto &e : p->graphs) R->graph_destroy(e.exec);
     p->graphs.clear();
-    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hi, p->ST32_lo, p->spec_unit,
+    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hl, p->spec_unit,
                     p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);
@@ -1115,8 +1113,7 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
     ca.N = N;
     ca.r = (int)p->r;
     ca.rpad = (int)p->rpad;
-    ca.ST_hi = p->ST32_hi;
-    ca.ST_lo = p->ST32_lo;
+    ca.ST_hl = p->ST32_hl;
     ca.pair0 = 0;
     ca.npairs = npairs;
     const int64_t nK = (N + CORR_BLOCK - 1) / CORR_BLOCK;

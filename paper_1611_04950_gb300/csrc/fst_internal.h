@@ -84,7 +84,7 @@ struct Runner {
   virtual fst_status gather_ST(const double *S, int64_t N, const int *sel, int r, int rpad, double *ST64,
                                float *ST32) = 0;
   virtual fst_status to_f32(const double *src, float *dst, int64_t n) = 0;
-  virtual fst_status split_tf32(const float *src, float *hi, float *lo, int64_t n) = 0;
+  virtual fst_status split_tf32(const float *src, float2 *hl, int64_t n) = 0;
 
   // fast coefficient vector kernels (runner memory)
   virtual fst_status coef_lowrank(const CoefArgs<float> &a) = 0;
@@ -130,7 +130,8 @@ struct fst_plan_s {
   double W = 0, eps = 0, alpha = 0, beta = 1;
   int op = 0;
   fst::Layout lay32, lay64;
-  float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr, *ST32_hi = nullptr, *ST32_lo = nullptr;
+  float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr;
+  float2 *ST32_hl = nullptr;  // TF32 (hi, lo) split of ST32, interleaved
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
   double *spec_unit = nullptr;   // plan-time only: DFT_M(c) / M for the eigenvalues
   float2 *tw32h = nullptr, *tw32l = nullptr;

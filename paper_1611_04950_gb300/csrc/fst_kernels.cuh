@@ -78,8 +78,7 @@ template <typename T> struct ConvArgs {
   // plan data
   const T *spec;      // DFT_M(c) * beta / M, natural order (small) or [k1][k2] (3-pass)
   const T *ST;        // [N][rpad], row n = (s_j[n])_j, zero padded
-  const T *ST_hi;     // FP32 fast path: TF32-rounded S_T and the TF32 remainder
-  const T *ST_lo;
+  const c2<T> *ST_hl; // FP32 tensor-core path: (TF32-rounded S_T, TF32 remainder) interleaved
   int r, rpad;
   const T *D;         // [r]
   Tw<T> tw;
