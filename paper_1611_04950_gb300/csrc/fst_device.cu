@@ -1,6 +1,8 @@
 // fst_device.cu -- CUDA back-end of the fast Slepian projection library (sm_103a):
 // the __global__ wrappers of the kernel bodies, the device Runner, and the
 // host-buffer entry point with overlapped copies.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -12,6 +14,8 @@
 
 #include "fst_internal.h"
 #include "fst_fast.cuh"
+#define FST_TC_KERNELS
+#include "fst_tc.cuh"
 
 namespace fst {
 
@@ -260,6 +264,11 @@ static fst_status cuda_fail(cudaError_t e, const char *what) {
     if (_e != cudaSuccess) return cuda_fail(_e, what);  \
   } while (0)
 #define LAUNCHED(what) CU(cudaGetLastError(), what)
+#define TRY(expr)                \
+  do {                           \
+    fst_status _s = (expr);      \
+    if (_s != FST_OK) return _s; \
+  } while (0)
 
 static bool g_attr_done = false;
 static fst_status set_attrs() {
@@ -275,6 +284,10 @@ static fst_status set_attrs() {
   CU(cudaFuncSetAttribute(k_passB<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passC<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passC<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_corr_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_corr_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_corr_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_corr_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   g_attr_done = true;
   return FST_OK;
 }
@@ -314,6 +327,39 @@ static void prof_end(cudaStream_t s, cudaEvent_t ea) {
 
 bool profiling_enabled() { return g_prof_on != 0; }
 
+// ---- TMA tensor maps (driver entry point, resolved once) --------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D FP32 tensor map: rows of `inner` elements `row_bytes` apart, box inner x outer
+static fst_status encode_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                            uint32_t box_inner, uint32_t box_outer, bool swizzle128) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(FST_ECUDA, "cuTensorMapEncodeTiled not available");
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(FST_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return FST_OK;
+}
+
 static inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
@@ -323,10 +369,13 @@ struct DevRunner : Runner {
   cudaStream_t s = nullptr;     // caller's stream
   cudaStream_t cur = nullptr;   // stream the apply kernels go to (s, or a capture lane)
   cudaStream_t cap[2] = {nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ev_mid = nullptr;
   bool capturing = false;
   long long launches_at_begin = 0;
+  int sms = 1;
+  int *tc_err = nullptr;   // raised by k_corr_tc when one of its waits timed out
   bool device() const override { return true; }
+  int sm_count() const override { return sms; }
   void set_stream(void *st) override { s = (cudaStream_t)st; cur = s; }
   void *stream() const override { return (void *)s; }
   ~DevRunner() override {
@@ -334,10 +383,22 @@ struct DevRunner : Runner {
       if (cap[i]) cudaStreamDestroy(cap[i]);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (ev_mid) cudaEventDestroy(ev_mid);
+    if (tc_err) cudaFree(tc_err);
   }
 
   int lanes() const override { return capturing ? 2 : 1; }
   void use_lane(int i) override { cur = capturing ? cap[i & 1] : s; }
+  void lanes_after_first() override {
+    if (!capturing) return;
+    cudaEventRecord(ev_mid, cap[0]);
+    cudaStreamWaitEvent(cap[1], ev_mid, 0);
+  }
+  void lanes_join_first() override {
+    if (!capturing) return;
+    cudaEventRecord(ev_mid, cap[1]);
+    cudaStreamWaitEvent(cap[0], ev_mid, 0);
+  }
   bool user_stream_capturing() override {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
@@ -351,7 +412,8 @@ struct DevRunner : Runner {
       for (int i = 0; i < 2; ++i)
         if (cudaStreamCreateWithFlags(&cap[i], cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return false; }
       if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_mid, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return false;
       }
@@ -501,6 +563,54 @@ struct DevRunner : Runner {
     dim3 grid((unsigned)((a.N + CORR_BLOCK - 1) / CORR_BLOCK), (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
     PROF("k_corr_c", a.npairs, (k_corr_c<<<grid, FAST_THREADS, 0, cur>>>(f)));
     LAUNCHED("k_corr_c");
+    return FST_OK;
+  }
+  fst_status tc_prep(const float2 *hl, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) override {
+    // plan time (never inside a stream capture): kernel attributes and the error word
+    TRY(set_attrs());
+    if (!tc_err) {
+      CU(cudaMalloc((void **)&tc_err, sizeof(int)), "cudaMalloc");
+      CU(cudaMemset(tc_err, 0, sizeof(int)), "cudaMemset");
+    }
+    k_tc_prep<<<grid_for((int64_t)nB * Npad, 256), 256, 0, s>>>(hl, N, rpad, r, nB, Npad, STt);
+    LAUNCHED("k_tc_prep");
+    return FST_OK;
+  }
+  fst_status corr_tc(const ConvArgs<float> &a) override {
+    if (!tc_err) return fail(FST_EUNSUPPORTED, "tcgen05 correction used before its plan-time set-up");
+    CUtensorMap mY, mS;
+    if (a.cplx)
+      TRY(encode_2d(&mY, a.y, 2 * (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 8, 2 * TC_KT, TC_M / 2, false));
+    else
+      TRY(encode_2d(&mY, a.y, (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 4, TC_KT, TC_M, false));
+    TRY(encode_2d(&mS, a.STt, (uint64_t)a.N, 2 * (uint64_t)a.tc_nB, (uint64_t)a.tc_Npad * 4, TC_KT,
+                  (uint32_t)a.tc_nB, true));
+    TcArgs t{};
+    t.N = a.N;
+    t.rows = a.batch;
+    t.cplx = a.cplx;
+    t.nB = a.tc_nB;
+    t.r = a.r;
+    t.rpad = a.rpad;
+    t.ktiles = (int)((a.N + TC_KT - 1) / TC_KT);
+    t.nks = tc_slices(a.N);
+    const int64_t rb = a.cplx ? (a.batch + TC_M / 2 - 1) / (TC_M / 2) : (a.batch + TC_M - 1) / TC_M;
+    if ((int64_t)t.nks * rb >= (1LL << 31)) return fail(FST_EINVAL, "batch too large for the tcgen05 correction");
+    t.nitems = (int)(t.nks * rb);
+    t.stages = a.tc_nB <= 96 ? 3 : 2;
+    t.part = a.part;
+    t.err = tc_err;
+    // persistent: one CTA per SM walks the items
+    dim3 grid((unsigned)std::min<int64_t>(t.nitems, sms));
+    const size_t smem = (size_t)tc_smem_bytes(t.nB, t.stages);
+    switch (t.nB) {
+      case 32: PROF("k_corr_tc", a.npairs, (k_corr_tc<32><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
+      case 64: PROF("k_corr_tc", a.npairs, (k_corr_tc<64><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
+      case 96: PROF("k_corr_tc", a.npairs, (k_corr_tc<96><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
+      case 128: PROF("k_corr_tc", a.npairs, (k_corr_tc<128><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
+      default: return fail(FST_EINVAL, "tcgen05 correction width out of range");
+    }
+    LAUNCHED("k_corr_tc");
     return FST_OK;
   }
   fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) override {
@@ -668,7 +778,12 @@ Runner *make_dev_runner() {
     cudaGetLastError();
     return nullptr;
   }
-  return new DevRunner();
+  DevRunner *R = new DevRunner();
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&R->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  if (R->sms < 1) R->sms = 1;
+  return R;
 }
 
 }  // namespace fst

@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
   const int64_t tile = blockIdx.x, g0 = (int64_t)blockIdx.y * FAST_G;
   const int64_t n2 = tile * FAST_NB + c;
   const bool live = (g0 + g) < a.npairs;
-  const bool corr = a.mode == MODE_FULL && a.r > 0;
+  const bool corr = (a.mode == MODE_FULL || a.mode == MODE_ZONLY) && a.r > 0;
 
   if (corr) {
     const int lane = c, gid = lane >> 2, tig = lane & 3;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 2) k_corr_c(const FastArgs f) {
 // a[pair][c][j] = scale_j * sum over row blocks of the partials: warp per output,
 // lanes stride the blocks, fixed xor-tree across lanes (deterministic)
 __global__ void k_corr_reduce(const ConvArgs<float> a, const float *scale) {
-  const int nK = (int)((a.N + CORR_BLOCK - 1) / CORR_BLOCK);
+  const int nK = a.nkb;
   const int64_t pl = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = w; t < 2 * a.r; t += nw) {

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fst_internal.h"
+#include "fst_tc.cuh"
 #include "../../include/fst_testing.h"
 
 namespace fst {
@@ -116,10 +117,36 @@ static size_t ws_need(const Layout &L, bool dbl, int rpad, bool forward) {
 // bytes of one launch group's scratch (one lane)
 static size_t slot_bytes(const Layout &L, bool dbl, int rpad, bool forward) { return ws_need(L, dbl, rpad, forward); }
 
-// scratch of the separate correction for npairs pairs (partials per CORR_BLOCK + a)
+// scratch of the separate correction for npairs pairs (partials per CORR_BLOCK rows or per
+// tcgen05 slice, then a)
 static size_t split_corr_bytes(int64_t N, int64_t npairs, int rpad) {
-  const int64_t nK = (N + CORR_BLOCK - 1) / CORR_BLOCK;
+  const int64_t nK = std::max<int64_t>((N + CORR_BLOCK - 1) / CORR_BLOCK, tc_slices(N));
   return (size_t)npairs * (nK + 1) * 2 * std::max(rpad, 1) * sizeof(float) + 256;
+}
+
+static bool tc_disabled() {
+  const char *s = getenv("FST_TC");
+  return s && s[0] == '0';
+}
+
+// the tcgen05 correction applies: FP32 device plan with K-major S_T^T tiles and signal rows
+// a TMA tensor map can address (16-byte aligned base and row stride)
+static bool tc_usable(const ConvArgs<float> &a) {
+  if (!a.STt || tc_disabled()) return false;
+  const int64_t row_bytes = a.ld * (a.cplx ? 8 : 4);
+  return ((uintptr_t)a.y % 16) == 0 && row_bytes % 16 == 0 && a.N < (1LL << 30) && a.batch < (1LL << 31);
+}
+
+// S_T^T y for every pair into sc.part, then a = scale o (sum of the partials) into sc.acoef
+static fst_status corr_coefficients(Runner *R, ConvArgs<float> &sc, const float *scale) {
+  if (tc_usable(sc)) {
+    sc.nkb = tc_slices(sc.N);
+    TRY(R->corr_tc(sc));
+  } else {
+    sc.nkb = (int)((sc.N + CORR_BLOCK - 1) / CORR_BLOCK);
+    TRY(R->corr_c(sc));
+  }
+  return R->corr_reduce(sc, scale);
 }
 
 template <typename T>
@@ -135,21 +162,26 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   const int64_t M = 1LL << L.log2M;
   const int lanes = R->lanes();
   const size_t slot = slot_bytes(L, sizeof(T) == 8, a.rpad, a.mode == MODE_FORWARD);
-  // separate tensor-core correction (FP32 device, P > 32): S_T^T y over every pair
-  // first (before any output is written, so y == out works), out += S_T a at the end
-  const bool split = L.split_corr && a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device();
+  // separate correction (FP32 device): a = D o S_T^T y over every pair first (before any
+  // output is written, so y == out works); on tcgen05 whenever the signal rows allow a
+  // tensor map, else mma.sync kernels for P > 32.  Then out += S_T a: in the fast column
+  // pass C, or by a last kernel over the whole batch.
+  const bool want = a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device() && !L.small;
+  const bool tc = want && tc_usable(*reinterpret_cast<const ConvArgs<float> *>(&a));
+  const bool split = want && (L.split_corr || tc);
   ConvArgs<float> sc{};
   if (split) {
     sc = *reinterpret_cast<const ConvArgs<float> *>(&a);
     char *w = (char *)ws + (size_t)lanes * slot;
-    const int64_t nK = (a.N + CORR_BLOCK - 1) / CORR_BLOCK;
+    const int64_t nK = std::max<int64_t>((a.N + CORR_BLOCK - 1) / CORR_BLOCK, tc_slices(a.N));
     sc.pair0 = 0;
     sc.npairs = npairs;
     sc.part = (float *)w;
     sc.acoef = (float *)(w + (size_t)npairs * nK * 2 * a.rpad * sizeof(float));
-    TRY(R->corr_c(sc));
-    TRY(R->corr_reduce(sc, (const float *)a.D));
-    a.mode = MODE_CONV;
+    TRY(corr_coefficients(R, sc, (const float *)a.D));
+    a.mode = L.fast ? MODE_ZONLY : MODE_CONV;
+    // every launch group, on either lane, runs after the coefficients
+    R->lanes_after_first();
   }
   int64_t group = 0;
   for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk, ++group) {
@@ -161,6 +193,7 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
       const size_t inter_b = (size_t)L.chunk * M * sizeof(C);
       a.part = (T *)(w + inter_b);
       a.acoef = (T *)(w + inter_b + (size_t)L.chunk * L.ntiles * 2 * std::max(a.rpad, 1) * sizeof(T));
+      if (a.mode == MODE_ZONLY) a.acoef = (T *)(sc.acoef + (size_t)p0 * 2 * a.rpad);
     }
     a.pair0 = p0;
     a.npairs = std::min<int64_t>(L.chunk, npairs - p0);
@@ -174,7 +207,11 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     }
   }
   R->use_lane(0);
-  if (split) TRY(R->corr_z(sc));
+  if (split && !L.fast) {
+    // out += S_T a over the whole batch once both lanes have written B y
+    R->lanes_join_first();
+    TRY(R->corr_z(sc));
+  }
   return FST_OK;
 }
 
@@ -215,6 +252,9 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.ST = ST;
   if (sizeof(T) == 4) {
     a.ST_hl = (const c2<T> *)p->ST32_hl;
+    a.STt = p->STt;
+    a.tc_nB = p->tc_nB;
+    a.tc_Npad = p->tc_Npad;
   }
   a.r = full ? (int)p->r : 0;
   a.rpad = (int)p->rpad;
@@ -223,7 +263,8 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
   a.mode = full ? MODE_FULL : MODE_CONV;
   const int64_t npairs = cplx ? batch : (batch + 1) / 2;
   const bool dbl = sizeof(T) == 8;
-  const size_t extra = (L0.split_corr && full && p->r > 0) ? split_corr_bytes(p->N, npairs, (int)p->rpad) : 0;
+  const bool sep = (L0.split_corr || (p->STt && !L0.small && !dbl)) && full && p->r > 0;
+  const size_t extra = sep ? split_corr_bytes(p->N, npairs, (int)p->rpad) : 0;
   if (!ext_ws) {
     Runner *R = p->R;
     // launch groups no larger than the call needs (small batches, ragged signals)
@@ -654,6 +695,17 @@ static fst_status plan_end(fst_plan_t p, double *S, const std::vector<double> &l
   }
   p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad, R->device());
   p->lay64 = make_layout(N, p->log2M, true, (int)p->rpad, false);
+  if (R->device() && !p->lay32.small && p->r > 0 && p->r <= 128) {
+    // K-major TF32 (hi, lo) tiles of S_T^T for the tcgen05 correction
+    fst_status s;
+    p->tc_nB = (int)((p->r + 31) / 32 * 32);
+    p->tc_Npad = (N + 3) / 4 * 4;
+    const size_t nt = 2 * (size_t)p->tc_nB * p->tc_Npad;
+    if ((s = R->alloc((void **)&p->STt, nt * sizeof(float))) != FST_OK) return bail(s);
+    if ((s = R->tc_prep(p->ST32_hl, N, (int)p->rpad, (int)p->r, p->tc_nB, p->tc_Npad, p->STt)) != FST_OK)
+      return bail(s);
+    if ((s = R->sync()) != FST_OK) return bail(s);
+  }
   if (p->lay32.small && p->lay32.smem_small > 227 * 1024)
     return bail(fail(FST_EUNSUPPORTED, "transition rank too large for the single-CTA path"));
   if (p->lay64.small && p->lay64.smem_small > 227 * 1024)
@@ -723,7 +775,7 @@ void destroy_plan(fst_plan_t p) {
     R->sync();
     for (auto &e : p->graphs) R->graph_destroy(e.exec);
     p->graphs.clear();
-    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hl, p->spec_unit,
+    void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hl, p->STt, p->spec_unit,
                     p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);
@@ -1116,11 +1168,13 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
     ca.ST_hl = p->ST32_hl;
     ca.pair0 = 0;
     ca.npairs = npairs;
-    const int64_t nK = (N + CORR_BLOCK - 1) / CORR_BLOCK;
+    ca.STt = p->STt;
+    ca.tc_nB = p->tc_nB;
+    ca.tc_Npad = p->tc_Npad;
+    const int64_t nK = std::max<int64_t>((N + CORR_BLOCK - 1) / CORR_BLOCK, tc_slices(N));
     ca.part = (float *)c.partU;
     ca.acoef = (float *)c.partU + (size_t)npairs * nK * 2 * p->rpad;
-    TRY(R->corr_c(ca));
-    TRY(R->corr_reduce(ca, (const float *)sq));
+    TRY(corr_coefficients(R, ca, (const float *)sq));
     c.upairs = 1;
     c.acoefU = (const T *)ca.acoef;
   } else if (p->r > 0) {

@@ -35,6 +35,10 @@ struct Runner {
   virtual bool user_stream_capturing() { return false; }
   virtual int lanes() const { return 1; }
   virtual void use_lane(int) {}
+  // order lane 1 after everything lane 0 has issued so far
+  virtual void lanes_after_first() {}
+  // order lane 0 after everything lane 1 has issued so far
+  virtual void lanes_join_first() {}
   virtual fst_status alloc(void **p, size_t bytes) = 0;
   virtual void release(void *p) = 0;
   virtual fst_status h2d(void *dst, const void *src, size_t bytes) = 0;
@@ -60,6 +64,12 @@ struct Runner {
                                   const Layout &L) = 0;
   // separate correction (FP32, device): partials, reduce to a = D o c, out += S_T a
   virtual fst_status corr_c(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  // tcgen05 S_T^T y over every pair of a (a.pair0 = 0): partials [pair][a.nkb][2][rpad]
+  virtual fst_status corr_tc(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  virtual fst_status tc_prep(const float2 *hl, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) {
+    return FST_EUNSUPPORTED;
+  }
+  virtual int sm_count() const { return 1; }
   virtual fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) { return FST_EUNSUPPORTED; }
   virtual fst_status corr_z(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
 
@@ -132,6 +142,9 @@ struct fst_plan_s {
   fst::Layout lay32, lay64;
   float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr;
   float2 *ST32_hl = nullptr;  // TF32 (hi, lo) split of ST32, interleaved
+  float *STt = nullptr;       // K-major TF32 hi/lo tiles of S_T^T for the tcgen05 correction
+  int tc_nB = 0;
+  int64_t tc_Npad = 0;
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
   double *spec_unit = nullptr;   // plan-time only: DFT_M(c) / M for the eigenvalues
   float2 *tw32h = nullptr, *tw32l = nullptr;

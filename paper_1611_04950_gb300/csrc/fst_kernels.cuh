@@ -32,7 +32,8 @@
 
 namespace fst {
 
-enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2 };
+// MODE_ZONLY: B y + S_T a with a = D o S_T^T y computed beforehand (fast column passes)
+enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2, MODE_ZONLY = 3 };
 
 constexpr int CORR_ROWS = 512;    // samples per tensor-core tile of the separate correction kernels
 constexpr int CORR_BLOCK = 2048;  // samples per partial sum of S_T^T y (four tiles)
@@ -87,6 +88,10 @@ template <typename T> struct ConvArgs {
   T *part;            // [npairs][ntiles][2][rpad]
   T *acoef;           // [npairs][2][rpad]: D o c for (re, im)
   int mode;
+  int nkb;            // partial blocks per pair summed by the separate correction's reduction
+  const float *STt;   // FP32 device plans: S_T^T as K-major TF32 (hi, lo) tiles, [2 tc_nB][tc_Npad]
+  int tc_nB;
+  int64_t tc_Npad;
 };
 
 // TF32 rounding (round to nearest, ties away from zero, 10 mantissa bits kept)

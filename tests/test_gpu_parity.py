@@ -188,7 +188,11 @@ def test_strided_inplace_and_host_entry_point():
                   torch.cuda.current_stream().cuda_stream)
     dense = p.project(view.contiguous())
     torch.cuda.synchronize()
-    assert torch.equal(out[:, :N], dense)
+    # rows N + 7 floats apart are not 16-byte aligned, so no TMA tensor map can address them:
+    # that call sums S_T^T y on the mma.sync kernels instead of tcgen05 (another summation
+    # order, same FP32 accuracy)
+    scale = dense.abs().max().item()
+    assert (out[:, :N] - dense).abs().max().item() <= 2e-6 * scale
     assert torch.all(out[:, N:] == 0)
     host = view.contiguous().cpu().pin_memory()
     hout = p.project_host(host)
