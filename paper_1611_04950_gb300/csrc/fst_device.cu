@@ -565,26 +565,27 @@ struct DevRunner : Runner {
     LAUNCHED("k_corr_c");
     return FST_OK;
   }
-  fst_status tc_prep(const float2 *hl, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) override {
+  fst_status tc_prep(const float *ST, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) override {
     // plan time (never inside a stream capture): kernel attributes and the error word
     TRY(set_attrs());
     if (!tc_err) {
       CU(cudaMalloc((void **)&tc_err, sizeof(int)), "cudaMalloc");
       CU(cudaMemset(tc_err, 0, sizeof(int)), "cudaMemset");
     }
-    k_tc_prep<<<grid_for((int64_t)nB * Npad, 256), 256, 0, s>>>(hl, N, rpad, r, nB, Npad, STt);
+    k_tc_prep<<<grid_for((int64_t)nB * Npad, 256), 256, 0, s>>>(ST, N, rpad, r, nB, Npad, STt);
     LAUNCHED("k_tc_prep");
     return FST_OK;
   }
   fst_status corr_tc(const ConvArgs<float> &a) override {
     if (!tc_err) return fail(FST_EUNSUPPORTED, "tcgen05 correction used before its plan-time set-up");
     CUtensorMap mY, mS;
+    // y in 128-byte swizzled boxes: 32 floats of 128 rows (real) or of 64 complex rows
     if (a.cplx)
-      TRY(encode_2d(&mY, a.y, 2 * (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 8, 2 * TC_KT, TC_M / 2, false));
+      TRY(encode_2d(&mY, a.y, 2 * (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 8, TC_KT, TC_M / 2, true));
     else
-      TRY(encode_2d(&mY, a.y, (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 4, TC_KT, TC_M, false));
-    TRY(encode_2d(&mS, a.STt, (uint64_t)a.N, 2 * (uint64_t)a.tc_nB, (uint64_t)a.tc_Npad * 4, TC_KT,
-                  (uint32_t)a.tc_nB, true));
+      TRY(encode_2d(&mY, a.y, (uint64_t)a.N, (uint64_t)a.batch, (uint64_t)a.ld * 4, TC_KT, TC_M, true));
+    TRY(encode_2d(&mS, a.STt, (uint64_t)a.N, (uint64_t)a.tc_nB, (uint64_t)a.tc_Npad * 4, TC_KT, (uint32_t)a.tc_nB,
+                  true));
     TcArgs t{};
     t.N = a.N;
     t.rows = a.batch;
@@ -597,12 +598,11 @@ struct DevRunner : Runner {
     const int64_t rb = a.cplx ? (a.batch + TC_M / 2 - 1) / (TC_M / 2) : (a.batch + TC_M - 1) / TC_M;
     if ((int64_t)t.nks * rb >= (1LL << 31)) return fail(FST_EINVAL, "batch too large for the tcgen05 correction");
     t.nitems = (int)(t.nks * rb);
-    t.stages = a.tc_nB <= 96 ? 3 : 2;
     t.part = a.part;
     t.err = tc_err;
     // persistent: one CTA per SM walks the items
     dim3 grid((unsigned)std::min<int64_t>(t.nitems, sms));
-    const size_t smem = (size_t)tc_smem_bytes(t.nB, t.stages);
+    const size_t smem = (size_t)tc_smem_bytes(t.nB);
     switch (t.nB) {
       case 32: PROF("k_corr_tc", a.npairs, (k_corr_tc<32><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
       case 64: PROF("k_corr_tc", a.npairs, (k_corr_tc<64><<<grid, TC_THREADS, smem, cur>>>(mY, mS, t))); break;
@@ -614,7 +614,8 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) override {
-    PROF("k_corr_reduce", a.npairs, (k_corr_reduce<<<(unsigned)a.npairs, 256, 0, cur>>>(a, scale)));
+    dim3 grid((unsigned)a.npairs, (unsigned)((2 * a.r + 7) / 8));
+    PROF("k_corr_reduce", a.npairs, (k_corr_reduce<<<grid, 256, 0, cur>>>(a, scale)));
     LAUNCHED("k_corr_reduce");
     return FST_OK;
   }

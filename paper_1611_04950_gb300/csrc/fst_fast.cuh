@@ -528,11 +528,12 @@ __global__ void __launch_bounds__(FAST_THREADS, 2) k_corr_c(const FastArgs f) {
 
 // a[pair][c][j] = scale_j * sum over row blocks of the partials: warp per output,
 // lanes stride the blocks, fixed xor-tree across lanes (deterministic)
+// grid (pairs, ceil(2 r / warps)): one warp per (pair, component, j), lanes over the blocks
 __global__ void k_corr_reduce(const ConvArgs<float> a, const float *scale) {
   const int nK = a.nkb;
   const int64_t pl = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = w; t < 2 * a.r; t += nw) {
+  for (int t = blockIdx.y * nw + w; t < 2 * a.r; t += nw * gridDim.y) {
     const int c = t / a.r, j = t % a.r;
     float s = 0.f;
     for (int b = lane; b < nK; b += 32) s += a.part[((pl * nK + b) * 2 + c) * a.rpad + j];

@@ -696,13 +696,13 @@ static fst_status plan_end(fst_plan_t p, double *S, const std::vector<double> &l
   p->lay32 = make_layout(N, p->log2M, false, (int)p->rpad, R->device());
   p->lay64 = make_layout(N, p->log2M, true, (int)p->rpad, false);
   if (R->device() && !p->lay32.small && p->r > 0 && p->r <= 128) {
-    // K-major TF32 (hi, lo) tiles of S_T^T for the tcgen05 correction
+    // K-major FP32 S_T^T for the tcgen05 correction
     fst_status s;
     p->tc_nB = (int)((p->r + 31) / 32 * 32);
     p->tc_Npad = (N + 3) / 4 * 4;
-    const size_t nt = 2 * (size_t)p->tc_nB * p->tc_Npad;
+    const size_t nt = (size_t)p->tc_nB * p->tc_Npad;
     if ((s = R->alloc((void **)&p->STt, nt * sizeof(float))) != FST_OK) return bail(s);
-    if ((s = R->tc_prep(p->ST32_hl, N, (int)p->rpad, (int)p->r, p->tc_nB, p->tc_Npad, p->STt)) != FST_OK)
+    if ((s = R->tc_prep(p->ST32, N, (int)p->rpad, (int)p->r, p->tc_nB, p->tc_Npad, p->STt)) != FST_OK)
       return bail(s);
     if ((s = R->sync()) != FST_OK) return bail(s);
   }

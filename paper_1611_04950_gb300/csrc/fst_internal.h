@@ -66,7 +66,7 @@ struct Runner {
   virtual fst_status corr_c(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
   // tcgen05 S_T^T y over every pair of a (a.pair0 = 0): partials [pair][a.nkb][2][rpad]
   virtual fst_status corr_tc(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
-  virtual fst_status tc_prep(const float2 *hl, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) {
+  virtual fst_status tc_prep(const float *ST, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) {
     return FST_EUNSUPPORTED;
   }
   virtual int sm_count() const { return 1; }
@@ -142,7 +142,7 @@ struct fst_plan_s {
   fst::Layout lay32, lay64;
   float *spec32 = nullptr, *ST32 = nullptr, *D32 = nullptr;
   float2 *ST32_hl = nullptr;  // TF32 (hi, lo) split of ST32, interleaved
-  float *STt = nullptr;       // K-major TF32 hi/lo tiles of S_T^T for the tcgen05 correction
+  float *STt = nullptr;       // S_T^T, K-major FP32 [tc_nB][tc_Npad], for the tcgen05 correction
   int tc_nB = 0;
   int64_t tc_Npad = 0;
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;

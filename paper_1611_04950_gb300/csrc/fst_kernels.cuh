@@ -89,7 +89,7 @@ template <typename T> struct ConvArgs {
   T *acoef;           // [npairs][2][rpad]: D o c for (re, im)
   int mode;
   int nkb;            // partial blocks per pair summed by the separate correction's reduction
-  const float *STt;   // FP32 device plans: S_T^T as K-major TF32 (hi, lo) tiles, [2 tc_nB][tc_Npad]
+  const float *STt;   // FP32 device plans: S_T^T, K-major, [tc_nB][tc_Npad]
   int tc_nB;
   int64_t tc_Npad;
 };

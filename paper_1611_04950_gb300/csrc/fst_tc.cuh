@@ -6,19 +6,26 @@
 //
 //   rows    : 128 real signals, or the (re, im) rows of 64 complex signals (MMA M = 128)
 //   columns : j < nB (MMA N = nB, a multiple of 32 covering r; rows j >= r of S are zero)
-//   K       : slices of TC_SLICE k-tiles of 32 samples; the CTAs walk the (row block, slice)
-//             items round-robin with one continuous pipeline and store one partial per item,
-//             so the summation order depends on N only, not on the batch or the grid
+//   K       : nks = tc_slices(N) interleaved slices of k-tiles of 32 samples (slice s takes
+//             k-tiles s, s + nks, s + 2 nks, ...); the CTAs walk the (row block, slice) items
+//             round-robin with one continuous pipeline and store one partial per item, so the
+//             summation order depends on N only, not on the batch or the grid.  Neighbouring
+//             CTAs read neighbouring 128-byte pieces of the same rows at the same time, which
+//             the DRAM serves as long runs.
 //
-// Each k-tile of y arrives by TMA (no swizzle) into a raw buffer; four worker warps split it
-// into TF32 (hi, lo) parts written in the 128-byte-swizzled K-major layout the MMA reads,
-// de-interleaving complex samples on the way.  S_T^T is stored K-major at plan time as
-// TF32 hi and lo parts and arrives by TMA already swizzled.  One thread issues, per 8-sample
-// k-step, the three products hi*hi + hi*lo + lo*hi into an FP32 accumulator in TMEM (the
-// missing lo*lo term is below FP32 rounding).  Every TC_GROUP k-tiles the epilogue warps
-// read the accumulator with tcgen05.ld into FP32 registers while the MMA fills a second
-// accumulator; at the end each stores one partial row per (signal, slice), and a separate
-// fixed-order reduction sums the slices, so results do not depend on scheduling.
+// Each k-tile of y arrives by TMA, 128-byte swizzled, in a ring of raw buffers together
+// with the k-tile of S_T^T (stored K-major in FP32 at plan time).  Eight worker warps split
+// both into TF32 (hi, lo) parts: each thread reads its own row of y (conflict-free thanks to
+// the swizzle), de-interleaving complex samples, and writes hi and lo straight into tensor
+// memory with tcgen05.st, where the MMA takes its A operand; S hi and lo go to a small
+// shared-memory ring as the B operand.  Keeping A out of shared memory matters: each TF32
+// MMA has K = 8 only, and with A in shared memory its operand fetch, not the tensor core,
+// set the pace.  One thread issues, per 8-sample k-step, the three products
+// hi*hi + hi*lo + lo*hi into FP32 accumulators in TMEM (the missing lo*lo term is below FP32
+// rounding).  Every TC_GROUP k-tiles the worker warps read the accumulators with
+// tcgen05.ld into FP32 registers while the MMA fills a second set; each item ends with one
+// partial row per (signal, slice), and a separate fixed-order reduction sums the slices, so
+// results do not depend on scheduling.
 //
 // Every mbarrier wait is bounded (TC_TIMEOUT_NS of wall time): on expiry the CTA stops
 // issuing work, waits (again bounded) for the copies and products it already issued,
@@ -31,8 +38,10 @@ namespace fst {
 
 constexpr int TC_M = 128;                 // MMA rows
 constexpr int TC_KT = 32;                 // samples per k-tile (128 bytes of FP32 per row)
-constexpr int TC_THREADS = 192;           // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-5 split + epilogue
-constexpr int TC_SLICE = 16;              // k-tiles per slice (512 samples)
+constexpr int TC_WORKERS = 8;             // split + drain warps (two per TMEM lane quarter)
+constexpr int TC_THREADS = 64 + 32 * TC_WORKERS;   // warp 0 TMA, warp 1 MMA + TMEM owner, then the workers
+constexpr int TC_SLICE_MIN = 16;          // k-tiles per slice at least (512 samples)
+constexpr int TC_SLICES_MAX = 1024;       // slices per signal at most
 constexpr int TC_RAW_BYTES = TC_M * TC_KT * 4;   // 16 KB: one k-tile of y
 constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
 
@@ -43,28 +52,52 @@ struct TcArgs {
   int nB;          // MMA N (32, 64, 96 or 128)
   int r, rpad;     // partial rows hold rpad floats, the first r meaningful
   int ktiles;      // ceil(N / TC_KT)
-  int nks;         // slices: ceil(ktiles / TC_SLICE)
+  int nks;         // interleaved slices
   int nitems;      // nks x row blocks
-  int stages;      // pipeline depth (2 or 3)
   float *part;     // [pair][nks][2][rpad]
   int *err;        // set to 1 when a wait timed out
 };
 
-// bytes of one pipeline stage: raw y tile, hi tile, lo tile, S hi and lo tiles
-__host__ __device__ constexpr int tc_stage_bytes(int nB) { return 3 * TC_RAW_BYTES + 2 * nB * 128; }
-__host__ __device__ constexpr int tc_smem_bytes(int nB, int stages) { return stages * tc_stage_bytes(nB) + 256 + 1024; }
-// two accumulator buffers of nB columns, allocated as a power of two >= 32
-__host__ __device__ constexpr uint32_t tc_tmem_cols(int nB) { return 2 * nB <= 32 ? 32u : (2 * nB <= 64 ? 64u : (2 * nB <= 128 ? 128u : 256u)); }
+// raw ring stage (shared memory): y tile + S tile; operand stage: S hi + S lo in shared
+// memory, y hi + y lo in TMEM (2 TC_KT columns)
+__host__ __device__ constexpr int tc_op_depth(int nB) { return nB == 64 ? 2 : 3; }
+__host__ __device__ constexpr int tc_raw_stage(int nB) { return TC_RAW_BYTES + nB * 128; }
+__host__ __device__ constexpr int tc_op_stage(int nB) { return 2 * nB * 128; }
+__host__ __device__ constexpr int tc_raw_depth(int nB) {
+  return nB <= 32 ? 8 : (nB <= 64 ? 7 : (nB <= 96 ? 5 : 4));
+}
+__host__ __device__ constexpr int tc_smem_bytes(int nB) {
+  return tc_raw_depth(nB) * tc_raw_stage(nB) + tc_op_depth(nB) * tc_op_stage(nB) + 512 + 1024;
+}
+// Each tcgen05.mma costs a roughly fixed time when it is as small as these (K = 8), so the
+// count matters more than the size.  For nB <= 64 the S hi and lo tiles, adjacent in shared
+// memory, form one B operand of 2 nB rows: one MMA gives hi*hi and hi*lo side by side, a
+// second lo*hi, into three nB-column accumulators (nacc = 3).  Wider S falls back to three
+// MMAs into one accumulator.  TMEM: op-depth A stages of 2 TC_KT columns, then 2 buffers of
+// nacc x nB columns.
+__host__ __device__ constexpr int tc_nacc(int nB) { return nB <= 64 ? 3 : 1; }
+constexpr uint32_t TC_TMEM_COLS = 512;
+static_assert(3 * 2 * TC_KT + 2 * 3 * 32 <= 512 && 2 * 2 * TC_KT + 2 * 3 * 64 <= 512 &&
+                  3 * 2 * TC_KT + 2 * 128 <= 512,
+              "TMEM budget");
 
 // instruction descriptor of tcgen05.mma kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, shape M x N
+// K-major, shape M x N (A in tensor memory is K-major by construction)
 __host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// slices of the sample axis for signal length N
+// k-tiles per slice of the sample axis for signal length N (even: whole MMA groups), and
+// the number of slices; both depend on N only
+__host__ __device__ inline int tc_slice_len(int64_t N) {
+  const int64_t kt = (N + TC_KT - 1) / TC_KT;
+  int64_t L = (kt + TC_SLICES_MAX - 1) / TC_SLICES_MAX;
+  L = L < TC_SLICE_MIN ? TC_SLICE_MIN : L;
+  return (int)((L + 1) / 2 * 2);
+}
 __host__ __device__ inline int tc_slices(int64_t N) {
-  return (int)(((N + TC_KT - 1) / TC_KT + TC_SLICE - 1) / TC_SLICE);
+  const int64_t kt = (N + TC_KT - 1) / TC_KT;
+  return (int)((kt + tc_slice_len(N) - 1) / tc_slice_len(N));
 }
 
 // kernels: compiled only in the translation unit that launches them
@@ -141,39 +174,59 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 32 consecutive accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v) {
-  uint32_t u[32];
+// A operand from tensor memory (`a` = TMEM address of its first column), B from shared memory
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
-        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
-        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
-        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
+// 16 consecutive TMEM columns of this thread's lane (no wait)
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tc_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ float tc_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// 16 consecutive accumulator columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t *u) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tc_hi(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
 
 // TMEM accumulation is coarser than FP32 round-to-nearest, so each accumulator buffer holds
 // only TC_GROUP k-tiles (TC_GROUP x 4 x 3 accumulation steps); the epilogue warps drain it
 // into FP32 registers while the MMA fills the other buffer.
 constexpr int TC_GROUP = 2;
 
-// item it of a CTA: row block it / nks, slice it % nks, k-tiles [ks TC_SLICE, ...)
+// item it of a CTA: row block it / nks, slice ks = it % nks: k-tiles ks + tt nks, tt < ntile
 struct TcItem {
-  int rb, ks, kt0, ntile;
+  int rb, ks, ntile;
 };
 __device__ __forceinline__ TcItem tc_item(const TcArgs &t, int it) {
   TcItem x;
   x.rb = it / t.nks;
   x.ks = it % t.nks;
-  x.kt0 = x.ks * TC_SLICE;
-  x.ntile = min(TC_SLICE, t.ktiles - x.kt0);
+  x.ntile = (t.ktiles - x.ks + t.nks - 1) / t.nks;
   return x;
 }
 
@@ -184,34 +237,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(tc_smem);
   const uint32_t base = (s0 + 1023u) & ~1023u;        // 128-byte swizzle atoms need 1024-byte alignment
   uint8_t *gbase = tc_smem + (base - s0);
-  constexpr int SB = tc_stage_bytes(NB);
-  const int S = t.stages;
-  // barriers: full[s] (TMA landed), split[s] (hi/lo written), freeb[s] (products retired),
-  // accfull[b] (buffer b holds a finished group), accempty[b] (buffer b drained), done
-  const uint32_t bars = base + (uint32_t)(S * SB);
-  const uint32_t full0 = bars, split0 = bars + 32, free0 = bars + 64;
-  const uint32_t afull0 = bars + 96, aempty0 = bars + 112, done = bars + 128;
-  uint32_t *tslot = (uint32_t *)(gbase + S * SB + 136);
-  volatile int *abort_flag = (volatile int *)(gbase + S * SB + 140);
+  constexpr int SA = tc_raw_stage(NB), SO = tc_op_stage(NB), RA = tc_raw_depth(NB), RB = tc_op_depth(NB);
+  constexpr int NACC = tc_nacc(NB);
+  constexpr uint32_t ACC0 = RB * 2 * TC_KT;            // TMEM: A stages first, then the accumulators
+  const uint32_t opb = base + RA * SA;                 // S hi/lo ring
+  // barriers: fullA[a] (TMA landed), freeA[a] (raw read), fullB[b] (operands written),
+  // emptyB[b] (products retired), accfull[c], accempty[c] (accumulator buffer c), done
+  const uint32_t bars = opb + RB * SO;
+  const uint32_t fullA = bars, freeA = bars + 64, fullB = bars + 128, emptyB = bars + 160;
+  const uint32_t afull0 = bars + 192, aempty0 = bars + 208, done = bars + 224;
+  uint8_t *gbars = gbase + (bars - base);
+  uint32_t *tslot = (uint32_t *)(gbars + 232);
+  volatile int *abort_flag = (volatile int *)(gbars + 236);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr uint32_t ncols = tc_tmem_cols(NB);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      tc_mbar_init(full0 + 8 * s, 1);
-      tc_mbar_init(split0 + 8 * s, 4);
-      tc_mbar_init(free0 + 8 * s, 1);
+    for (int a = 0; a < RA; ++a) {
+      tc_mbar_init(fullA + 8 * a, 1);
+      tc_mbar_init(freeA + 8 * a, TC_WORKERS);
     }
-    for (int b = 0; b < 2; ++b) {
-      tc_mbar_init(afull0 + 8 * b, 1);
-      tc_mbar_init(aempty0 + 8 * b, 4);
+    for (int b = 0; b < RB; ++b) {
+      tc_mbar_init(fullB + 8 * b, TC_WORKERS);
+      tc_mbar_init(emptyB + 8 * b, 1);
+    }
+    for (int c = 0; c < 2; ++c) {
+      tc_mbar_init(afull0 + 8 * c, 1);
+      tc_mbar_init(aempty0 + 8 * c, TC_WORKERS);
     }
     tc_mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(bars + 136), "r"(ncols)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(bars + 232),
+                 "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -221,69 +280,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *tslot;
 
   if (warp == 0) {
-    // ---- producer: y tile + S hi/lo tiles per stage, item after item
+    // ---- producer: y tile (swizzled) + S tile per raw stage, item after item
     if (lane == 0) {
-      const uint32_t tx = (uint32_t)TC_RAW_BYTES + 256u * (uint32_t)NB;
       int i = 0, issued = 0;
       bool go = true;
       for (int it = blockIdx.x; it < t.nitems && go; it += gridDim.x) {
         const TcItem x = tc_item(t, it);
         for (int tt = 0; tt < x.ntile; ++tt, ++i) {
-          const int s = i % S;
-          if (i >= S && !tc_wait(free0 + 8 * s, (uint32_t)((i / S) - 1) & 1u, abort_flag, true)) {
+          const int a = i % RA;
+          if (i >= RA && !tc_wait(freeA + 8 * a, (uint32_t)((i / RA) - 1) & 1u, abort_flag, true)) {
             go = false;
             break;
           }
-          const uint32_t st = base + (uint32_t)(s * SB);
-          tc_mbar_expect_tx(full0 + 8 * s, tx);
-          const int kt = x.kt0 + tt;
-          if (t.cplx) tc_tma_2d(st, &tmY, full0 + 8 * s, kt * 2 * TC_KT, x.rb * (TC_M / 2));
-          else tc_tma_2d(st, &tmY, full0 + 8 * s, kt * TC_KT, x.rb * TC_M);
-          tc_tma_2d(st + 3 * TC_RAW_BYTES, &tmS, full0 + 8 * s, kt * TC_KT, 0);
-          tc_tma_2d(st + 3 * TC_RAW_BYTES + 128 * NB, &tmS, full0 + 8 * s, kt * TC_KT, NB);
+          const uint32_t st = base + (uint32_t)(a * SA);
+          tc_mbar_expect_tx(fullA + 8 * a, (uint32_t)SA);
+          const int kt = x.ks + tt * t.nks;
+          if (t.cplx) {
+            // two halves of 16 complex samples (128 bytes per row each)
+            tc_tma_2d(st, &tmY, fullA + 8 * a, kt * 2 * TC_KT, x.rb * (TC_M / 2));
+            tc_tma_2d(st + TC_RAW_BYTES / 2, &tmY, fullA + 8 * a, kt * 2 * TC_KT + TC_KT, x.rb * (TC_M / 2));
+          } else {
+            tc_tma_2d(st, &tmY, fullA + 8 * a, kt * TC_KT, x.rb * TC_M);
+          }
+          tc_tma_2d(st + TC_RAW_BYTES, &tmS, fullA + 8 * a, kt * TC_KT, 0);
           issued = i + 1;
         }
       }
       // the copies issued last must land before the CTA may exit
-      for (int j = max(0, issued - S); j < issued; ++j)
-        tc_wait(full0 + 8 * (j % S), (uint32_t)(j / S) & 1u, abort_flag, false);
+      for (int j = max(0, issued - RA); j < issued; ++j)
+        tc_wait(fullA + 8 * (j % RA), (uint32_t)(j / RA) & 1u, abort_flag, false);
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer: groups of TC_GROUP k-tiles of one item into accumulator buffer g & 1
     if (lane == 0) {
       const uint32_t idesc = tc_idesc_tf32(TC_M, NB);
+      const uint32_t idesc2 = tc_idesc_tf32(TC_M, 2 * NB);   // B = [S hi; S lo]
       int i = 0, g = 0;
       bool go = true;
       for (int it = blockIdx.x; it < t.nitems && go; it += gridDim.x) {
         const TcItem x = tc_item(t, it);
         for (int tt = 0; tt < x.ntile; ++tt, ++i) {
-          const int s = i % S, b = g & 1;
+          const int b = i % RB, c = g & 1;
           const bool first = (tt % TC_GROUP) == 0;
-          if (first && g >= 2 && !tc_wait(aempty0 + 8 * b, (uint32_t)((g / 2) - 1) & 1u, abort_flag, true)) {
+          if (first && g >= 2 && !tc_wait(aempty0 + 8 * c, (uint32_t)((g / 2) - 1) & 1u, abort_flag, true)) {
             go = false;
             break;
           }
-          if (!tc_wait(split0 + 8 * s, (uint32_t)(i / S) & 1u, abort_flag, true)) {
+          if (!tc_wait(fullB + 8 * b, (uint32_t)(i / RB) & 1u, abort_flag, true)) {
             go = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = base + (uint32_t)(s * SB);
-          const uint32_t ah = st + TC_RAW_BYTES, al = st + 2 * TC_RAW_BYTES;
-          const uint32_t bh = st + 3 * TC_RAW_BYTES, bl = bh + 128 * NB;
-          const uint32_t acc = tmem + (uint32_t)(b * NB);
+          const uint32_t ahi = tmem + (uint32_t)(b * 2 * TC_KT), alo = ahi + TC_KT;
+          const uint32_t bh = opb + (uint32_t)(b * SO);
+          const uint32_t acc = tmem + ACC0 + (uint32_t)(c * NACC * NB);
+          // a k-step of 8 samples is 32 bytes along the 128-byte rows: +2 in the address field
+          const uint64_t dbh = tc_desc_sw128(bh), dbl = tc_desc_sw128(bh + 128 * NB);
 #pragma unroll
           for (int k = 0; k < TC_KT / 8; ++k) {
-            const uint64_t dah = tc_desc_sw128(ah + 32 * k), dal = tc_desc_sw128(al + 32 * k);
-            const uint64_t dbh = tc_desc_sw128(bh + 32 * k), dbl = tc_desc_sw128(bl + 32 * k);
-            tc_mma(acc, dah, dbh, idesc, (first && k == 0) ? 0u : 1u);
-            tc_mma(acc, dah, dbl, idesc, 1u);
-            tc_mma(acc, dal, dbh, idesc, 1u);
+            const uint32_t fresh = (first && k == 0) ? 0u : 1u;
+            if (NACC == 3) {
+              tc_mma_ts(acc, ahi + 8 * k, dbh + 2 * k, idesc2, fresh);
+              tc_mma_ts(acc + 2 * NB, alo + 8 * k, dbh + 2 * k, idesc, fresh);
+            } else {
+              tc_mma_ts(acc, ahi + 8 * k, dbh + 2 * k, idesc, fresh);
+              tc_mma_ts(acc, ahi + 8 * k, dbl + 2 * k, idesc, 1u);
+              tc_mma_ts(acc, alo + 8 * k, dbh + 2 * k, idesc, 1u);
+            }
           }
-          tc_commit(free0 + 8 * s);
+          tc_commit(emptyB + 8 * b);
           if ((tt % TC_GROUP) == TC_GROUP - 1 || tt == x.ntile - 1) {
-            tc_commit(afull0 + 8 * b);
+            tc_commit(afull0 + 8 * c);
             ++g;
           }
         }
@@ -293,13 +361,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- workers: TF32 split into the swizzled K-major hi/lo tiles; drains; partials
-    const int tw = threadIdx.x - 64;
-    const int q = warp & 3;   // TMEM lane quarter of this warp: rows 32 q + lane
+    // ---- workers: TF32 split of y (rows into TMEM) and S (shared); drains; partials
+    constexpr int NH = NB / 2;        // accumulator columns drained by this warp
+    const int tw = threadIdx.x - 64;  // 0 .. 32 TC_WORKERS - 1
+    const int q = warp & 3;           // TMEM lane quarter of this warp: rows 32 q + lane
+    const int h = (warp - 2) >> 2;    // samples [16 h, 16 h + 16) of a k-tile; columns [h NH, (h + 1) NH)
     const int m = 32 * q + lane;
-    float sum[NB];
+    const uint32_t lq = (uint32_t)(32 * q) << 16;
+    float sum[NH];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) sum[j] = 0.f;
+    for (int j = 0; j < NH; ++j) sum[j] = 0.f;
     bool ok = true;
     // store the partial row of item it (NaN after an abort) and restart the sums
     auto flush = [&](int it) {
@@ -318,31 +389,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // real: the partner of an odd last signal gets its (zero) row too
       const bool valid = t.cplx ? sig < t.rows : pair < (t.rows + 1) / 2;
       if (valid) {
-        float *dst = t.part + ((pair * t.nks + x.ks) * 2 + comp) * t.rpad;
+        float *dst = t.part + ((pair * t.nks + x.ks) * 2 + comp) * t.rpad + h * NH;
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-          if (j < t.rpad) dst[j] = ok ? sum[j] : __int_as_float(0x7fc00000);
+        for (int j = 0; j < NH; ++j)
+          if (h * NH + j < t.rpad) dst[j] = ok ? sum[j] : __int_as_float(0x7fc00000);
       }
 #pragma unroll
-      for (int j = 0; j < NB; ++j) sum[j] = 0.f;
+      for (int j = 0; j < NH; ++j) sum[j] = 0.f;
     };
     // add finished group g (of item it; the item's last group if `last`) into the sums
     auto drain = [&](int g, int it, bool last) {
-      const int b = g & 1;
-      if (ok) ok = tc_wait(afull0 + 8 * b, (uint32_t)(g / 2) & 1u, abort_flag, true);
+      const int c = g & 1;
+      if (ok) ok = tc_wait(afull0 + 8 * c, (uint32_t)(g / 2) & 1u, abort_flag, true);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
         tc_fence_after();
+        uint32_t u[NACC][NH];
 #pragma unroll
-        for (int cb = 0; cb < NB / 32; ++cb) {
-          float v[32];
-          tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * NB + 32 * cb), v);
+        for (int ac = 0; ac < NACC; ++ac)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[32 * cb + j] += v[j];
+          for (int cb = 0; cb < NH / 16; ++cb)
+            tc_ld16(tmem + lq + ACC0 + (uint32_t)((c * NACC + ac) * NB + h * NH + 16 * cb), &u[ac][16 * cb]);
+        tc_ld_wait();
+        // fixed order: the accumulators, then into the running sum
+#pragma unroll
+        for (int j = 0; j < NH; ++j) {
+          float g0 = __uint_as_float(u[0][j]);
+#pragma unroll
+          for (int ac = 1; ac < NACC; ++ac) g0 += __uint_as_float(u[ac][j]);
+          sum[j] += g0;
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) tc_mbar_arrive(aempty0 + 8 * b);
+        if (lane == 0) tc_mbar_arrive(aempty0 + 8 * c);
       }
       if (last) flush(it);
     };
@@ -352,46 +431,66 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int it = blockIdx.x; it < t.nitems; it += gridDim.x) {
       const TcItem x = tc_item(t, it);
       for (int tt = 0; tt < x.ntile; ++tt, ++i) {
-        const int s = i % S;
-        if (ok) ok = tc_wait(full0 + 8 * s, (uint32_t)(i / S) & 1u, abort_flag, true);
+        const int a = i % RA, b = i % RB;
+        if (ok) ok = tc_wait(fullA + 8 * a, (uint32_t)(i / RA) & 1u, abort_flag, true);
+        if (ok && i >= RB) ok = tc_wait(emptyB + 8 * b, (uint32_t)((i / RB) - 1) & 1u, abort_flag, true);
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
-          uint8_t *st = gbase + s * SB;
-          const float4 *raw = (const float4 *)st;
-          uint8_t *hi = st + TC_RAW_BYTES, *lo = st + 2 * TC_RAW_BYTES;
+          tc_fence_after();
+          const uint8_t *ra = gbase + a * SA;
+          float v[16];
           if (!t.cplx) {
-            // raw: [128 rows][32 floats]; 16-byte chunk c of row r goes to chunk c ^ (r & 7)
+            // row m, samples 16 h .. 16 h + 15: chunks 4 h .. 4 h + 3, chunk c stored at c ^ (m & 7)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int qq = k * 128 + tw;
-              const int r = qq >> 3, c = qq & 7;
-              const float4 v = raw[qq];
-              const float4 h = make_float4(tc_hi(v.x), tc_hi(v.y), tc_hi(v.z), tc_hi(v.w));
-              const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-              const int off = r * 128 + ((c ^ (r & 7)) << 4);
-              *(float4 *)(hi + off) = h;
-              *(float4 *)(lo + off) = l;
+            for (int k = 0; k < 4; ++k) {
+              const int c = 4 * h + k;
+              const float4 f = *(const float4 *)(ra + m * 128 + ((c ^ (m & 7)) << 4));
+              v[4 * k] = f.x;
+              v[4 * k + 1] = f.y;
+              v[4 * k + 2] = f.z;
+              v[4 * k + 3] = f.w;
             }
           } else {
-            // raw: [64 rows][32 complex]; real parts to row r, imaginary parts to row 64 + r
+            // row m: part m >> 6 (re, im) of signal m & 63; half h holds complex samples 16 h ..
+            const int sg = m & 63;
+            const bool im = m >= 64;
+            const uint8_t *hb = ra + h * (TC_RAW_BYTES / 2) + sg * 128;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int qq = k * 128 + tw;
-              const int r = qq >> 4, cc = qq & 15;
-              const float4 v = raw[qq];   // (re, im) of samples 2 cc and 2 cc + 1
-              const int sub = (cc & 1) * 8, c = cc >> 1;
-              const int offr = r * 128 + ((c ^ (r & 7)) << 4) + sub;
-              const int offi = offr + 64 * 128;   // (r + 64) & 7 == r & 7
-              const float2 hr = make_float2(tc_hi(v.x), tc_hi(v.z)), hm = make_float2(tc_hi(v.y), tc_hi(v.w));
-              *(float2 *)(hi + offr) = hr;
-              *(float2 *)(lo + offr) = make_float2(v.x - hr.x, v.z - hr.y);
-              *(float2 *)(hi + offi) = hm;
-              *(float2 *)(lo + offi) = make_float2(v.y - hm.x, v.w - hm.y);
+            for (int c = 0; c < 8; ++c) {
+              const float4 f = *(const float4 *)(hb + ((c ^ (sg & 7)) << 4));
+              v[2 * c] = im ? f.y : f.x;
+              v[2 * c + 1] = im ? f.w : f.z;
             }
           }
+          float vh[16], vl[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            vh[j] = tc_hi(v[j]);
+            vl[j] = v[j] - vh[j];
+          }
+          const uint32_t acol = (uint32_t)(b * 2 * TC_KT + 16 * h);
+          tc_st16(tmem + lq + acol, vh);
+          tc_st16(tmem + lq + acol + TC_KT, vl);
+          // S tile: already swizzled by the TMA; hi and lo keep its layout
+          constexpr int NS = NB * 8 / (32 * TC_WORKERS);
+          const float4 *sraw = (const float4 *)(ra + TC_RAW_BYTES);
+          float4 *shi = (float4 *)(gbase + (opb - base) + b * SO), *slo = shi + NB * 8;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const int qq = k * 32 * TC_WORKERS + tw;
+            const float4 sv = sraw[qq];
+            const float4 hs = make_float4(tc_hi(sv.x), tc_hi(sv.y), tc_hi(sv.z), tc_hi(sv.w));
+            shi[qq] = hs;
+            slo[qq] = make_float4(sv.x - hs.x, sv.y - hs.y, sv.z - hs.z, sv.w - hs.w);
+          }
+          tc_st_wait();
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          tc_fence_before();
           __syncwarp();
-          if (lane == 0) tc_mbar_arrive(split0 + 8 * s);
+          if (lane == 0) {
+            tc_mbar_arrive(freeA + 8 * a);
+            tc_mbar_arrive(fullB + 8 * b);
+          }
         }
         if ((tt % TC_GROUP) == TC_GROUP - 1 || tt == x.ntile - 1) {
           // group g is fully split: drain the group before it
@@ -410,24 +509,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) atomicExch(t.err, 1);
 }
 
-// S_T^T as K-major TF32 parts: STt[j][n] = hi, STt[nB + j][n] = lo (zero for j >= r, n >= N)
-__global__ void k_tc_prep(const float2 *hl, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) {
+// S_T^T in FP32, K-major: STt[j][n] (zero for j >= r, n >= N)
+__global__ void k_tc_prep(const float *ST, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) {
   const int64_t total = (int64_t)nB * Npad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / Npad);
     const int64_t n = e % Npad;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < r && n < N) v = hl[n * rpad + j];
-    STt[e] = v.x;
-    STt[(int64_t)nB * Npad + e] = v.y;
+    STt[e] = (j < r && n < N) ? ST[n * rpad + j] : 0.f;
   }
 }
 
 #endif  // __CUDACC__ && FST_TC_KERNELS
+
 
 }  // namespace fst
