@@ -538,9 +538,20 @@ struct DevRunner : Runner {
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
   fst_status passA(const ConvArgs<float> &a, const Layout &L) override {
     if (!L.fast) return passA_t(a, L);
+    const int P = 1 << L.log2P;
+    // no fused correction, real signals: 256-byte row loads when the rows allow float2 loads
+    // (measured faster for real rows, slower for complex ones)
+    const bool wide_ok = !a.cplx && (uintptr_t)a.y % 8 == 0 && a.ld % 2 == 0;
+    if (a.mode != MODE_FULL && wide_ok) {
+      dim3 grid((unsigned)((1 << L.log2Q) / FASTW_NB), (unsigned)((a.npairs + FASTW_G - 1) / FASTW_G));
+      if (P == 32) PROF("k_fastAw<32>", a.npairs, (k_fastAw<32><<<grid, FAST_THREADS, 0, cur>>>(a)));
+      else if (P == 16) PROF("k_fastAw<16>", a.npairs, (k_fastAw<16><<<grid, FAST_THREADS, 0, cur>>>(a)));
+      else PROF("k_fastAw<8>", a.npairs, (k_fastAw<8><<<grid, FAST_THREADS, 0, cur>>>(a)));
+      LAUNCHED("k_fastAw");
+      return FST_OK;
+    }
     FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
-    const int P = 1 << L.log2P;
     if (P == 32) PROF("k_fastA<32>", a.npairs, (k_fastA<32><<<grid, FAST_THREADS, 0, cur>>>(f)));
     else if (P == 16) PROF("k_fastA<16>", a.npairs, (k_fastA<16><<<grid, FAST_THREADS, 0, cur>>>(f)));
     else PROF("k_fastA<8>", a.npairs, (k_fastA<8><<<grid, FAST_THREADS, 0, cur>>>(f)));

@@ -89,6 +89,105 @@ template <bool INV> struct RegDft<32, INV> {
   }
 };
 
+// P-point DFT of column n2 (v), times W_M^{n2 k1}, stored to inter[row0 + k1 Q + n2].
+// k1 = 8h + b, W^{k1} = W^{8h} W^b: table lookups for W, W^8, W^16, small powers by at most
+// two products, applied and stored right away.
+template <int P>
+__device__ __forceinline__ void fastA_finish(const ConvArgs<float> &a, float2 *v, int64_t row0, int64_t n2) {
+  const int Q = 1 << a.log2Q;
+  RegDft<P, false>::run(v);
+  float2 *dst = a.inter + row0 + n2;
+  const float2 w1 = a.tw.root<false>((uint64_t)n2, a.log2M);
+  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
+  float2 wh[4];
+  wh[0] = make_float2(1.f, 0.f);
+  if (P > 8) wh[1] = a.tw.root<false>(8 * (uint64_t)n2, a.log2M);
+  if (P > 16) {
+    wh[2] = a.tw.root<false>(16 * (uint64_t)n2, a.log2M);
+    wh[3] = cmul(wh[2], wh[1]);
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int l = b & 3;
+    float2 wb = (l == 0) ? make_float2(1.f, 0.f) : (l == 1 ? w1 : (l == 2 ? w2 : w3));
+    if (b >= 4) wb = (l == 0) ? w4 : cmul(w4, wb);
+#pragma unroll
+    for (int h = 0; h < P / 8; ++h) {
+      const int k1 = 8 * h + b;
+      const float2 w = (h == 0) ? wb : (b == 0 ? wh[h] : cmul(wh[h], wb));
+      dst[(int64_t)k1 * Q] = (k1 == 0) ? v[0] : cmul(v[k1], w);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass A without the correction (B y alone, or a = D o S_T^T y computed beforehand):
+// tiles of FASTW_G pairs x FASTW_NB columns, so each warp load reads 256 contiguous bytes
+// of a signal row (DRAM serves few, long requests much faster than many 128-byte ones);
+// the tile is transposed through shared memory to one column per thread.
+// grid (Q / FASTW_NB, ceil(npairs / FASTW_G)), FAST_THREADS threads: warp w -> pair w / 2,
+// columns 32 (w & 1) + lane.  Rows: real signals need 8-byte, complex 16-byte aligned rows.
+// ---------------------------------------------------------------------------
+constexpr int FASTW_NB = 64, FASTW_G = 4;
+template <int P>
+__global__ void __launch_bounds__(FAST_THREADS, 3) k_fastAw(const ConvArgs<float> a) {
+  constexpr int R = P / 2;   // rows n1 that can hold samples (M >= 2N)
+  __shared__ __align__(16) float tile[2 * FASTW_G * R * FASTW_NB];
+  const int Q = 1 << a.log2Q;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g0 = (int64_t)blockIdx.y * FASTW_G;
+  const int64_t col0 = (int64_t)blockIdx.x * FASTW_NB;
+  if (!a.cplx) {
+    // rows (signal s of 2 FASTW_G, n1): 64 floats, one float2 per lane
+#pragma unroll
+    for (int k = 0; k < 2 * FASTW_G * R / 8; ++k) {
+      const int row = w + 8 * k;
+      const int s = row / R, n1 = row % R;
+      const int64_t sig = 2 * (a.pair0 + g0) + s;
+      const int64_t n = (int64_t)n1 * Q + col0 + 2 * lane;
+      float2 v = make_float2(0.f, 0.f);
+      if (sig < a.batch && 2 * (g0 + (s >> 1)) < 2 * a.npairs && n1 < a.Pnz) {
+        const float *src = a.y + sig * a.ld + n;
+        if (n + 1 < a.N) v = __ldg((const float2 *)src);
+        else if (n < a.N) v.x = __ldg(src);
+      }
+      *(float2 *)&tile[row * FASTW_NB + 2 * lane] = v;
+    }
+  } else {
+    // rows (pair p of FASTW_G, n1): 64 complex, two per lane
+    const float2 *y2 = reinterpret_cast<const float2 *>(a.y);
+#pragma unroll
+    for (int k = 0; k < FASTW_G * R / 8; ++k) {
+      const int row = w + 8 * k;
+      const int pp = row / R, n1 = row % R;
+      const int64_t n = (int64_t)n1 * Q + col0 + 2 * lane;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g0 + pp < a.npairs && n1 < a.Pnz) {
+        const float2 *src = y2 + (a.pair0 + g0 + pp) * a.ld + n;
+        if (n + 1 < a.N) v = __ldg((const float4 *)src);
+        else if (n < a.N) {
+          const float2 u = __ldg(src);
+          v.x = u.x;
+          v.y = u.y;
+        }
+      }
+      *(float4 *)&tile[(row * FASTW_NB + 2 * lane) * 2] = v;
+    }
+  }
+  __syncthreads();
+  const int pl = w >> 1, c = 32 * (w & 1) + lane;
+  if (g0 + pl >= a.npairs) return;
+  float2 v[P];
+#pragma unroll
+  for (int n1 = 0; n1 < P; ++n1) v[n1] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int n1 = 0; n1 < R; ++n1) {
+    if (!a.cplx) v[n1] = make_float2(tile[((2 * pl) * R + n1) * FASTW_NB + c], tile[((2 * pl + 1) * R + n1) * FASTW_NB + c]);
+    else v[n1] = reinterpret_cast<const float2 *>(tile)[(pl * R + n1) * FASTW_NB + c];
+  }
+  fastA_finish<P>(a, v, (g0 + pl) * P * (int64_t)Q, col0 + c);
+}
+
 // ---------------------------------------------------------------------------
 // pass A: load columns, correction partials (tensor cores), P-point DFT, twiddle
 // grid (ntiles, ngroups), FAST_THREADS threads; thread = (pair g = warp, column c = lane)
@@ -119,31 +218,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastA(const FastArgs f) {
   }
 
   if (live) {
-  RegDft<P, false>::run(v);
-  // times W_M^{n2 k1}: k1 = 8h + b, W^{k1} = W^{8h} W^b; table lookups for W, W^8, W^16,
-  // small powers by at most two products, applied and stored right away
-  float2 *dst = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
-  const float2 w1 = a.tw.root<false>((uint64_t)n2, a.log2M);
-  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
-  float2 wh[4];
-  wh[0] = make_float2(1.f, 0.f);
-  if (P > 8) wh[1] = a.tw.root<false>(8 * (uint64_t)n2, a.log2M);
-  if (P > 16) {
-    wh[2] = a.tw.root<false>(16 * (uint64_t)n2, a.log2M);
-    wh[3] = cmul(wh[2], wh[1]);
-  }
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int l = b & 3;
-    float2 wb = (l == 0) ? make_float2(1.f, 0.f) : (l == 1 ? w1 : (l == 2 ? w2 : w3));
-    if (b >= 4) wb = (l == 0) ? w4 : cmul(w4, wb);
-#pragma unroll
-    for (int h = 0; h < P / 8; ++h) {
-      const int k1 = 8 * h + b;
-      const float2 w = (h == 0) ? wb : (b == 0 ? wh[h] : cmul(wh[h], wb));
-      dst[(int64_t)k1 * Q] = (k1 == 0) ? v[0] : cmul(v[k1], w);
-    }
-  }
+  fastA_finish<P>(a, v, (g0 + g) * P * (int64_t)Q, n2);
   }
   if (corr) {
     __syncthreads();
