@@ -66,31 +66,38 @@ template <typename T> FST_HD c2<T> coef_sample(const CoefArgs<T> &a, int64_t sig
   return mk<T>(a.y[sig * a.ld + n], (T)0);
 }
 
-// Block-wide fixed-order reduction of every thread's acc[0 .. 2*cnt) into dst[0 .. 2*cnt):
-// red: nthr * 2 * COEF_GROUP reals of shared memory.
+// Block-wide fixed-order reduction of every thread's acc[0 .. 2*cnt) into dst[0 .. 2*cnt).
+// red: COEF_RED_WORDS reals of shared memory, laid out [q][COEF_RED_LD] (the thread values,
+// rows padded by 16 so that both passes below are free of bank conflicts), then
+// [q][COEF_RED_PARTS] part sums; dst may be red + COEF_RED_DST.  Part p of value q sums the
+// thread values p, p + 16, p + 32, ... in that order; then the parts are summed in order.
+constexpr int COEF_RED_PARTS = 16;
+constexpr int COEF_RED_LD = COEF_THREADS + 16;
+constexpr int COEF_RED_DST = 2 * COEF_GROUP * COEF_RED_LD + 2 * COEF_GROUP * COEF_RED_PARTS;
+constexpr int COEF_RED_WORDS = COEF_RED_DST + 2 * COEF_GROUP;
+static_assert(2 * COEF_GROUP * COEF_RED_PARTS <= COEF_THREADS, "one thread per (value, part)");
 template <typename T, typename Ex>
 FST_HD void coef_block_reduce(Ex &ex, T *red, int cnt, T *dst) {
   using St = typename Ex::State;
-  const int nthr = ex.nthr;
   ex.phase([&](int tid, St &st) {
 #pragma unroll
     for (int q = 0; q < 2 * COEF_GROUP; ++q)
-      if (q < 2 * cnt) red[q * nthr + tid] = st.acc[q];
+      if (q < 2 * cnt) red[q * COEF_RED_LD + tid] = st.acc[q];
   });
   ex.phase([&](int tid, St &) {
-    // thread (q, part): 8 parts of nthr / 8 values each, then the parts in order
-    const int parts = 8, span = nthr / parts;
-    if (tid < 2 * cnt * parts) {
-      const int q = tid / parts, pidx = tid % parts;
+    const int q = tid / COEF_RED_PARTS, pidx = tid % COEF_RED_PARTS;
+    if (q < 2 * cnt) {
       T s = 0;
-      for (int t = pidx * span; t < (pidx + 1) * span; ++t) s += red[q * nthr + t];
-      red[2 * COEF_GROUP * nthr + q * parts + pidx] = s;
+#pragma unroll
+      for (int i = 0; i < COEF_THREADS / COEF_RED_PARTS; ++i) s += red[q * COEF_RED_LD + pidx + COEF_RED_PARTS * i];
+      red[2 * COEF_GROUP * COEF_RED_LD + q * COEF_RED_PARTS + pidx] = s;
     }
   });
   ex.phase([&](int tid, St &) {
     if (tid < 2 * cnt) {
       T s = 0;
-      for (int pidx = 0; pidx < 8; ++pidx) s += red[2 * COEF_GROUP * nthr + tid * 8 + pidx];
+      for (int pidx = 0; pidx < COEF_RED_PARTS; ++pidx)
+        s += red[2 * COEF_GROUP * COEF_RED_LD + tid * COEF_RED_PARTS + pidx];
       dst[tid] = s;
     }
   });
@@ -162,9 +169,9 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
           }
         });
         T res[2 * COEF_GROUP];
-        coef_block_reduce<T>(ex, red, 2 * kc, red + 2 * COEF_GROUP * nthr + 16 * 8);
+        coef_block_reduce<T>(ex, red, 2 * kc, red + COEF_RED_DST);
         ex.phase([&](int tid, St &) {
-          const T *r = red + 2 * COEF_GROUP * nthr + 16 * 8;
+          const T *r = red + COEF_RED_DST;
           if (tid < kc) {
             const int k = k0 + tid;
             out[2 * (obase + k)] = r[4 * tid + 0];                 // sum Z v
@@ -198,9 +205,9 @@ FST_HD void coef_lowrank_body(Ex &ex, const CoefArgs<T> &a, int64_t sig, int chu
           }
         }
       });
-      coef_block_reduce<T>(ex, red, ic, red + 2 * COEF_GROUP * nthr + 16 * 8);
+      coef_block_reduce<T>(ex, red, ic, red + COEF_RED_DST);
       ex.phase([&](int tid, St &) {
-        const T *r = red + 2 * COEF_GROUP * nthr + 16 * 8;
+        const T *r = red + COEF_RED_DST;
         if (tid < ic) {
           out[2 * (obase + i0 + tid)] = r[2 * tid];
           out[2 * (obase + i0 + tid) + 1] = r[2 * tid + 1];

@@ -284,6 +284,9 @@ static fst_status set_attrs() {
   CU(cudaFuncSetAttribute(k_passB<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passC<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_passC<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
+  CU(cudaFuncSetAttribute(k_fastAw<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(32)), "attr");
+  CU(cudaFuncSetAttribute(k_fastAw<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(16)), "attr");
+  CU(cudaFuncSetAttribute(k_fastAw<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(8)), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
@@ -543,10 +546,12 @@ struct DevRunner : Runner {
     // (measured faster for real rows, slower for complex ones)
     const bool wide_ok = !a.cplx && (uintptr_t)a.y % 8 == 0 && a.ld % 2 == 0;
     if (a.mode != MODE_FULL && wide_ok) {
-      dim3 grid((unsigned)((1 << L.log2Q) / FASTW_NB), (unsigned)((a.npairs + FASTW_G - 1) / FASTW_G));
-      if (P == 32) PROF("k_fastAw<32>", a.npairs, (k_fastAw<32><<<grid, FAST_THREADS, 0, cur>>>(a)));
-      else if (P == 16) PROF("k_fastAw<16>", a.npairs, (k_fastAw<16><<<grid, FAST_THREADS, 0, cur>>>(a)));
-      else PROF("k_fastAw<8>", a.npairs, (k_fastAw<8><<<grid, FAST_THREADS, 0, cur>>>(a)));
+      TRY(set_attrs());
+      const int64_t tiles = ((1 << L.log2Q) / FASTW_NB) * ((a.npairs + FASTW_G - 1) / FASTW_G);
+      const unsigned grid = (unsigned)std::min<int64_t>(tiles, 3 * (int64_t)sms);
+      if (P == 32) PROF("k_fastAw<32>", a.npairs, (k_fastAw<32><<<grid, FAST_THREADS, fastw_smem(32), cur>>>(a)));
+      else if (P == 16) PROF("k_fastAw<16>", a.npairs, (k_fastAw<16><<<grid, FAST_THREADS, fastw_smem(16), cur>>>(a)));
+      else PROF("k_fastAw<8>", a.npairs, (k_fastAw<8><<<grid, FAST_THREADS, fastw_smem(8), cur>>>(a)));
       LAUNCHED("k_fastAw");
       return FST_OK;
     }
@@ -622,6 +627,14 @@ struct DevRunner : Runner {
       default: return fail(FST_EINVAL, "tcgen05 correction width out of range");
     }
     LAUNCHED("k_corr_tc");
+    return FST_OK;
+  }
+  fst_status z_rmw(const ConvArgs<float> &a, const float *ST) override {
+    const int nsig = a.cplx ? ZR_ROWS / 2 : ZR_ROWS;
+    dim3 grid((unsigned)((a.N + ZR_N - 1) / ZR_N), (unsigned)((a.batch + nsig - 1) / nsig));
+    if (a.rpad <= 32) PROF("k_z_rmw", a.npairs, (k_z_rmw<32><<<grid, ZR_THREADS, 0, cur>>>(a, ST)));
+    else PROF("k_z_rmw", a.npairs, (k_z_rmw<64><<<grid, ZR_THREADS, 0, cur>>>(a, ST)));
+    LAUNCHED("k_z_rmw");
     return FST_OK;
   }
   fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) override {
@@ -710,7 +723,7 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
-    const size_t smem = (2 * COEF_GROUP * COEF_THREADS + 16 * 8 + 16) * sizeof(T);
+    const size_t smem = (size_t)COEF_RED_WORDS * sizeof(T);
     dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
     PROF("k_coef_lowrank", 0, (k_coef_lowrank<T><<<grid, COEF_THREADS, smem, cur>>>(a)));
     LAUNCHED("k_coef_lowrank");

@@ -215,7 +215,7 @@ struct EmuRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
-    std::vector<T> red(2 * COEF_GROUP * COEF_THREADS + 16 * 8 + 16);
+    std::vector<T> red(COEF_RED_WORDS);
     for (int64_t sig = 0; sig < a.batch; ++sig)
       for (int c = 0; c < a.nchunks; ++c) {
         HostEx<CState<T>> ex(COEF_THREADS);

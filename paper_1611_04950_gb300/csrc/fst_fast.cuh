@@ -121,71 +121,78 @@ __device__ __forceinline__ void fastA_finish(const ConvArgs<float> &a, float2 *v
 }
 
 // ---------------------------------------------------------------------------
-// pass A without the correction (B y alone, or a = D o S_T^T y computed beforehand):
-// tiles of FASTW_G pairs x FASTW_NB columns, so each warp load reads 256 contiguous bytes
-// of a signal row (DRAM serves few, long requests much faster than many 128-byte ones);
-// the tile is transposed through shared memory to one column per thread.
-// grid (Q / FASTW_NB, ceil(npairs / FASTW_G)), FAST_THREADS threads: warp w -> pair w / 2,
-// columns 32 (w & 1) + lane.  Rows: real signals need 8-byte, complex 16-byte aligned rows.
+// pass A without the correction (B y alone, or a = D o S_T^T y computed beforehand), real
+// signals: tiles of FASTW_G pairs x FASTW_NB columns, so each warp load reads 256 contiguous
+// bytes of a signal row; the tile is transposed through shared memory to one column per
+// thread.  Persistent CTAs walk the tiles with two shared-memory buffers: the cp.async copies
+// of the next tile are in flight while the current one is transformed, so the load latency
+// is not exposed once per tile.
+// grid: at most 3 CTAs per SM, FAST_THREADS threads (warp w -> pair w / 2, columns
+// 32 (w & 1) + lane); dynamic shared memory fastw_smem(P).  Rows need 8-byte alignment.
 // ---------------------------------------------------------------------------
 constexpr int FASTW_NB = 64, FASTW_G = 4;
+__host__ __device__ constexpr int fastw_tile_floats(int P) { return 2 * FASTW_G * (P / 2) * FASTW_NB; }
+__host__ __device__ constexpr int fastw_smem(int P) { return 2 * fastw_tile_floats(P) * 4; }
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <int P>
 __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastAw(const ConvArgs<float> a) {
   constexpr int R = P / 2;   // rows n1 that can hold samples (M >= 2N)
-  __shared__ __align__(16) float tile[2 * FASTW_G * R * FASTW_NB];
+  constexpr int TF = fastw_tile_floats(P);
+  extern __shared__ __align__(16) float wtile[];
   const int Q = 1 << a.log2Q;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g0 = (int64_t)blockIdx.y * FASTW_G;
-  const int64_t col0 = (int64_t)blockIdx.x * FASTW_NB;
-  if (!a.cplx) {
-    // rows (signal s of 2 FASTW_G, n1): 64 floats, one float2 per lane
+  const int ncol = Q / FASTW_NB;
+  const int64_t ngrp = (a.npairs + FASTW_G - 1) / FASTW_G;
+  const int64_t total = ngrp * ncol;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wtile);
+  // copies of tile t into buffer b: rows (signal s of 2 FASTW_G, n1), 64 floats, 8 bytes a lane;
+  // samples past N or absent signals read as zero
+  auto issue = [&](int64_t t, int b) {
+    const int64_t g0 = (t / ncol) * FASTW_G;
+    const int64_t col0 = (t % ncol) * FASTW_NB;
 #pragma unroll
     for (int k = 0; k < 2 * FASTW_G * R / 8; ++k) {
       const int row = w + 8 * k;
       const int s = row / R, n1 = row % R;
       const int64_t sig = 2 * (a.pair0 + g0) + s;
       const int64_t n = (int64_t)n1 * Q + col0 + 2 * lane;
-      float2 v = make_float2(0.f, 0.f);
-      if (sig < a.batch && 2 * (g0 + (s >> 1)) < 2 * a.npairs && n1 < a.Pnz) {
-        const float *src = a.y + sig * a.ld + n;
-        if (n + 1 < a.N) v = __ldg((const float2 *)src);
-        else if (n < a.N) v.x = __ldg(src);
+      int bytes = 0;
+      const float *src = a.y;
+      if (sig < a.batch && g0 + (s >> 1) < a.npairs && n1 < a.Pnz && n < a.N) {
+        src = a.y + sig * a.ld + n;
+        bytes = (n + 1 < a.N) ? 8 : 4;
       }
-      *(float2 *)&tile[row * FASTW_NB + 2 * lane] = v;
+      cp_async8(sbase + (uint32_t)((b * TF + row * FASTW_NB + 2 * lane) * 4), src, bytes);
     }
-  } else {
-    // rows (pair p of FASTW_G, n1): 64 complex, two per lane
-    const float2 *y2 = reinterpret_cast<const float2 *>(a.y);
+  };
+  int64_t t = blockIdx.x;
+  if (t < total) issue(t, 0);
+  cp_async_commit();
+  for (int i = 0; t < total; ++i, t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < total) issue(tn, (i + 1) & 1);
+    cp_async_commit();
+    cp_async_wait1();   // this thread's copies of tile t have landed
+    __syncthreads();    // ... and everyone's
+    const float *tb = wtile + (i & 1) * TF;
+    const int64_t g0 = (t / ncol) * FASTW_G;
+    const int64_t col0 = (t % ncol) * FASTW_NB;
+    const int pl = w >> 1, c = 32 * (w & 1) + lane;
+    float2 v[P];
 #pragma unroll
-    for (int k = 0; k < FASTW_G * R / 8; ++k) {
-      const int row = w + 8 * k;
-      const int pp = row / R, n1 = row % R;
-      const int64_t n = (int64_t)n1 * Q + col0 + 2 * lane;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (g0 + pp < a.npairs && n1 < a.Pnz) {
-        const float2 *src = y2 + (a.pair0 + g0 + pp) * a.ld + n;
-        if (n + 1 < a.N) v = __ldg((const float4 *)src);
-        else if (n < a.N) {
-          const float2 u = __ldg(src);
-          v.x = u.x;
-          v.y = u.y;
-        }
-      }
-      *(float4 *)&tile[(row * FASTW_NB + 2 * lane) * 2] = v;
-    }
+    for (int n1 = 0; n1 < P; ++n1) v[n1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n1 = 0; n1 < R; ++n1)
+      v[n1] = make_float2(tb[((2 * pl) * R + n1) * FASTW_NB + c], tb[((2 * pl + 1) * R + n1) * FASTW_NB + c]);
+    __syncthreads();    // buffer i & 1 is refilled at the next iteration
+    if (g0 + pl < a.npairs) fastA_finish<P>(a, v, (g0 + pl) * P * (int64_t)Q, col0 + c);
   }
-  __syncthreads();
-  const int pl = w >> 1, c = 32 * (w & 1) + lane;
-  if (g0 + pl >= a.npairs) return;
-  float2 v[P];
-#pragma unroll
-  for (int n1 = 0; n1 < P; ++n1) v[n1] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int n1 = 0; n1 < R; ++n1) {
-    if (!a.cplx) v[n1] = make_float2(tile[((2 * pl) * R + n1) * FASTW_NB + c], tile[((2 * pl + 1) * R + n1) * FASTW_NB + c]);
-    else v[n1] = reinterpret_cast<const float2 *>(tile)[(pl * R + n1) * FASTW_NB + c];
-  }
-  fastA_finish<P>(a, v, (g0 + pl) * P * (int64_t)Q, col0 + c);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,6 +622,74 @@ __global__ void k_corr_reduce(const ConvArgs<float> a, const float *scale) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) a.acoef[(pl * 2 + c) * a.rpad + j] = __ldg(scale + j) * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// out += S_T a for every signal (the last step of the separate correction, a = D o S_T^T y
+// already summed): r <= RMAX FP32 FMAs per output value, on CUDA cores.
+// A block takes ZR_N consecutive samples and ZR_ROWS rows of a (real signals, or the (re, im)
+// rows of ZR_ROWS / 2 complex signals).  The S_T rows of its samples are contiguous in memory:
+// staged through shared memory with coalesced loads, then each thread keeps the row of its
+// sample in registers and walks half of the a rows (read as shared-memory broadcasts),
+// adding into out.  grid (ceil(N / ZR_N), ceil(rows / ZR_ROWS)), ZR_THREADS threads.
+// ---------------------------------------------------------------------------
+template <int RMAX>
+__global__ void __launch_bounds__(ZR_THREADS) k_z_rmw(const ConvArgs<float> a, const float *ST) {
+  __shared__ float st[ZR_N][RMAX + 1];
+  __shared__ float as[ZR_ROWS][RMAX];
+  const int r = a.r;
+  const int64_t n0 = (int64_t)blockIdx.x * ZR_N;
+  const int nsig = a.cplx ? ZR_ROWS / 2 : ZR_ROWS;
+  const int64_t sig0 = (int64_t)blockIdx.y * nsig;
+  // S_T rows n0 .. n0 + ZR_N - 1: ZR_N x rpad contiguous floats (rpad <= RMAX)
+  const int64_t nn = (a.N - n0 < ZR_N) ? a.N - n0 : ZR_N;
+  for (int t = threadIdx.x; t < ZR_N * a.rpad; t += ZR_THREADS) {
+    const int row = t / a.rpad, j = t % a.rpad;
+    st[row][j] = (row < nn && j < r) ? __ldg(ST + n0 * a.rpad + t) : 0.f;
+  }
+  for (int t = threadIdx.x; t < ZR_N * (RMAX - a.rpad); t += ZR_THREADS) {
+    const int row = t / (RMAX - a.rpad), j = a.rpad + t % (RMAX - a.rpad);
+    st[row][j] = 0.f;
+  }
+  // a rows: real signal sig0 + rr; complex signal sig0 + rr / 2, part rr & 1.  The rows of
+  // acoef are (pair 2 + part); for real signals that index is the signal itself.
+  for (int t = threadIdx.x; t < ZR_ROWS * RMAX; t += ZR_THREADS) {
+    const int rr = t / RMAX, j = t % RMAX;
+    const int64_t sg = a.cplx ? sig0 + rr / 2 : sig0 + rr;
+    const int64_t arow = a.cplx ? 2 * sg + (rr & 1) : sg;
+    as[rr][j] = (sg < a.batch && j < r) ? a.acoef[arow * a.rpad + j] : 0.f;
+  }
+  __syncthreads();
+  const int i = threadIdx.x % ZR_N, half = threadIdx.x / ZR_N;
+  const int64_t n = n0 + i;
+  if (n >= a.N) return;
+  float sv[RMAX];
+#pragma unroll
+  for (int j = 0; j < RMAX; ++j) sv[j] = st[i][j];
+  if (!a.cplx) {
+    const int rows = (int)(a.batch - sig0 < ZR_ROWS ? a.batch - sig0 : ZR_ROWS);
+    for (int rr = half; rr < rows; rr += 2) {
+      float z = 0.f;
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) z = fmaf(sv[j], as[rr][j], z);
+      a.out[(sig0 + rr) * a.ld + n] += z;
+    }
+  } else {
+    const int sigs = (int)(a.batch - sig0 < ZR_ROWS / 2 ? a.batch - sig0 : ZR_ROWS / 2);
+    for (int q = half; q < sigs; q += 2) {
+      float zr = 0.f, zi = 0.f;
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        zr = fmaf(sv[j], as[2 * q][j], zr);
+        zi = fmaf(sv[j], as[2 * q + 1][j], zi);
+      }
+      float2 *o = reinterpret_cast<float2 *>(a.out) + (sig0 + q) * a.ld + n;
+      float2 v = *o;
+      v.x += zr;
+      v.y += zi;
+      *o = v;
+    }
   }
 }
 

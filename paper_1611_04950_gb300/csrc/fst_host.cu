@@ -210,7 +210,12 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   if (split && !L.fast) {
     // out += S_T a over the whole batch once both lanes have written B y
     R->lanes_join_first();
-    TRY(R->corr_z(sc));
+    // CUDA-core pass when the batch has enough signal rows to share each staged S_T block
+    // (measured: faster from 64 rows up, slower for 16)
+    const int64_t zrows = sc.cplx ? 2 * sc.batch : sc.batch;
+    const bool zr_ok = sc.rpad <= 64 && zrows >= ZR_ROWS && (!sc.cplx || (uintptr_t)sc.out % 8 == 0);
+    if (zr_ok) TRY(R->z_rmw(sc, (const float *)a.ST));
+    else TRY(R->corr_z(sc));
   }
   return FST_OK;
 }

@@ -72,6 +72,8 @@ struct Runner {
   virtual int sm_count() const { return 1; }
   virtual fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) { return FST_EUNSUPPORTED; }
   virtual fst_status corr_z(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  // out += S_T a on CUDA cores (FP32, r <= 64)
+  virtual fst_status z_rmw(const ConvArgs<float> &a, const float *ST) { return FST_EUNSUPPORTED; }
 
   // plan kernels (all pointers in runner memory)
   virtual fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo,

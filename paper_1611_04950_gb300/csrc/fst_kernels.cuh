@@ -37,6 +37,8 @@ enum { MODE_FULL = 0, MODE_CONV = 1, MODE_FORWARD = 2, MODE_ZONLY = 3 };
 
 constexpr int CORR_ROWS = 512;    // samples per tensor-core tile of the separate correction kernels
 constexpr int CORR_BLOCK = 2048;  // samples per partial sum of S_T^T y (four tiles)
+// CUDA-core out += S_T a: threads, samples and signal rows per block
+constexpr int ZR_THREADS = 256, ZR_N = 128, ZR_ROWS = 64;
 
 // Launch layout of the length-M transform for one real type.
 struct Layout {
