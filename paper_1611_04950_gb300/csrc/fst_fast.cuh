@@ -297,24 +297,17 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastA(const FastArgs f) {
 // pass B for Q = 4096 = 16^3 (256 threads, 16 values per thread)
 // grid (P, npairs)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tw_stage16(const Tw<float> &tw, int k, int log2NsR, bool inv, float2 *x) {
-  // multiply x[t] by W_{Ns 16}^{k t}, t = 1..15
-  const uint32_t base = (uint32_t)k << (TW_LOG2 - log2NsR);
-  float2 w1 = inv ? tw.get<true>(base) : tw.get<false>(base);
-  float2 w4 = inv ? tw.get<true>(4 * base) : tw.get<false>(4 * base);
-  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-  const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
-  const float2 ws[4] = {make_float2(1.f, 0.f), w1, w2, w3};
-  const float2 wb[4] = {make_float2(1.f, 0.f), w4, w8, w12};
+// x[t] times W^{k t} (t = 1..15) from a [t][ldk] table (conjugated for the inverse):
+// lanes with consecutive k read consecutive entries
+__device__ __forceinline__ void tw_table16(const float2 *tab, int ldk, int k, bool inv, float2 *x) {
 #pragma unroll
   for (int t = 1; t < 16; ++t) {
-    const int lo = t & 3, hi = t >> 2;
-    float2 wt = (lo == 0) ? wb[hi] : (hi == 0 ? ws[lo] : cmul(wb[hi], ws[lo]));
-    x[t] = cmul(x[t], wt);
+    const float2 w = __ldg(tab + t * ldk + k);
+    x[t] = inv ? make_float2(x[t].x * w.x + x[t].y * w.y, x[t].y * w.x - x[t].x * w.y) : cmul(x[t], w);
   }
 }
 
-__global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
+__global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
   constexpr int Q = 4096, T = 256;
   __shared__ float2 buf[padded_size(Q)];
   const int P = 1 << a.log2P;
@@ -343,7 +336,7 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
   // stage 2 (Ns = 16)
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_stage16(a.tw, j & 15, 8, false, x);
+  tw_table16(a.twB, 16, j & 15, false, x);
   Dft<float, 16, false>::run(x);
   __syncthreads();
 #pragma unroll
@@ -352,7 +345,7 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
   // stage 3 (Ns = 256): outputs land at j + 256 t = natural k2
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_stage16(a.tw, j, 12, false, x);
+  tw_table16(a.twB + 256, 256, j, false, x);
   Dft<float, 16, false>::run(x);
   if (a.mode == MODE_FORWARD) {
 #pragma unroll
@@ -370,7 +363,7 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_stage16(a.tw, j & 15, 8, true, x);
+  tw_table16(a.twB, 16, j & 15, true, x);
   Dft<float, 16, true>::run(x);
   __syncthreads();
 #pragma unroll
@@ -378,7 +371,7 @@ __global__ void __launch_bounds__(256) k_fastB4096(const ConvArgs<float> a) {
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_stage16(a.tw, j, 12, true, x);
+  tw_table16(a.twB + 256, 256, j, true, x);
   Dft<float, 16, true>::run(x);
   // times W_M^{-n2 k1}, n2 = j + 256 t, straight to global memory
   const float2 wj = a.tw.root<true>((uint64_t)j * (uint64_t)k1, a.log2M);

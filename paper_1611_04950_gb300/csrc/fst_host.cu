@@ -260,6 +260,7 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
     a.STt = p->STt;
     a.tc_nB = p->tc_nB;
     a.tc_Npad = p->tc_Npad;
+    a.twB = p->twB;
   }
   a.r = full ? (int)p->r : 0;
   a.rpad = (int)p->rpad;
@@ -593,6 +594,19 @@ static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, in
     if ((s = R->h2d(p->tw64l, lo.data(), lo.size() * sizeof(double2))) != FST_OK) return bail(s);
     if ((s = R->h2d(p->tw32h, hi32.data(), hi32.size() * sizeof(float2))) != FST_OK) return bail(s);
     if ((s = R->h2d(p->tw32l, lo32.data(), lo32.size() * sizeof(float2))) != FST_OK) return bail(s);
+    std::vector<float2> tb(TWB_WORDS);
+    for (int t = 0; t < 16; ++t) {
+      for (int k = 0; k < 16; ++k) {
+        const double ang = -2.0 * M_PI * (double)(k * t) / 256.0;
+        tb[t * 16 + k] = make_float2((float)cos(ang), (float)sin(ang));
+      }
+      for (int k = 0; k < 256; ++k) {
+        const double ang = -2.0 * M_PI * (double)(k * t) / 4096.0;
+        tb[256 + t * 256 + k] = make_float2((float)cos(ang), (float)sin(ang));
+      }
+    }
+    if ((s = R->alloc((void **)&p->twB, tb.size() * sizeof(float2))) != FST_OK) return bail(s);
+    if ((s = R->h2d(p->twB, tb.data(), tb.size() * sizeof(float2))) != FST_OK) return bail(s);
   }
 
   Scoped sc(R);
@@ -781,7 +795,7 @@ void destroy_plan(fst_plan_t p) {
     for (auto &e : p->graphs) R->graph_destroy(e.exec);
     p->graphs.clear();
     void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hl, p->STt, p->spec_unit,
-                    p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->ws};
+                    p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->twB, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);
     delete R;

@@ -150,6 +150,9 @@ struct fst_plan_s {
   double *spec64 = nullptr, *ST64 = nullptr, *D64 = nullptr;
   double *spec_unit = nullptr;   // plan-time only: DFT_M(c) / M for the eigenvalues
   float2 *tw32h = nullptr, *tw32l = nullptr;
+  // stage twiddles of the 4096-point row FFT: [t][k] = W_256^{k t} (k < 16), then
+  // W_4096^{k t} (k < 256), t < 16
+  float2 *twB = nullptr;
   double2 *tw64h = nullptr, *tw64l = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;

@@ -94,7 +94,9 @@ template <typename T> struct ConvArgs {
   const float *STt;   // FP32 device plans: S_T^T, K-major, [tc_nB][tc_Npad]
   int tc_nB;
   int64_t tc_Npad;
+  const float2 *twB;  // FP32 device plans: stage twiddles of the 4096-point row FFT
 };
+constexpr int TWB_WORDS = 16 * 16 + 16 * 256;
 
 // TF32 rounding (round to nearest, ties away from zero, 10 mantissa bits kept)
 FST_HD float tf32_round(float x) {
