@@ -64,6 +64,21 @@ def make_workload(name, device, batch=None):
     raise ValueError(name)
 
 
+def ncu_traffic(kernel, pairs_per_launch):
+    """DRAM bytes (read + write) of one launch of `kernel`, from the ncu capture summarised in
+    profiles/ncu_traffic.txt (lines: kernel, bytes, pairs per captured launch), scaled to this
+    launch's pairs; None when that kernel has no capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel:
+                return float(parts[1]) * pairs_per_launch / float(parts[2])
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -347,14 +362,28 @@ def main():
     sig_bytes = N * (8 if y.is_complex() else 4)          # bytes of one signal
     pairs_per_launch = dd["pairs"] / dd["launches"]
     signals_per_launch = pairs_per_launch * (1 if y.is_complex() else 2)
-    alg_bytes = signals_per_launch * 2 * sig_bytes + N * plan.r * 4 + plan.M * 4
     launch_ms = dd["ms"] / dd["launches"]
-    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_source": peak_src,
-                "kernels": {k: {"launches": v["launches"] // 3, "ms_per_step": v["ms"] / 3,
-                                "share": v["ms"] / tot} for k, v in per.items()}}
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    log2M = int(round(math.log2(plan.M)))
+    log2Q = min(14, max(12, log2M - 5))
+    if dom.startswith("k_fastB") or dom.startswith("k_passB"):
+        # the row-FFT pass is bound by FP32 instruction issue: its share log2 Q / log2 M of the
+        # FFT flops, 5 M log2 Q per real signal (twice per complex one), per launch
+        flops = signals_per_launch * (2 if y.is_complex() else 1) * 5.0 * plan.M * log2Q
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "flops_per_launch": flops,
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x SM max clock"}
+    else:
+        alg_bytes = signals_per_launch * 2 * sig_bytes + N * plan.r * 4 + plan.M * 4
+        achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_src}
+    roofline["traffic"] = ncu_traffic(dom, pairs_per_launch)
+    roofline["kernel"] = dom
+    roofline["kernels"] = {k: {"launches": v["launches"] // 3, "ms_per_step": v["ms"] / 3,
+                               "share": v["ms"] / tot} for k, v in per.items()}
     # whole path against the same roofline (all kernels of one step)
     step_alg = B * 2 * sig_bytes + N * plan.r * 4 + plan.M * 4
     roofline["path_frac"] = step_alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
@@ -363,8 +392,6 @@ def main():
     # 8 N r per complex one); peak = SMs x 128 FP32 lanes x 2 flops x the maximum SM clock
     cf = 2 if y.is_complex() else 1
     flops = B * cf * (5.0 * plan.M * math.log2(plan.M) + 4.0 * N * plan.r)
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     alu_ach = flops / (ms * 1e-3) / 1e12
     roofline["alu"] = {"achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
                        "flops_per_step": flops, "peak_source": f"{sms} SMs x 128 lanes x 2 x SM max clock"}
