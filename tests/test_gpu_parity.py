@@ -141,6 +141,29 @@ def test_complex_signals():
     assert np.all(rel_err(out64, fast, y.numpy()) < 1e-5)
 
 
+def test_wide_transition_band_real_and_complex():
+    # r ~ 69 > 64: the tcgen05 correction's wide-S variant (nB = 96, one accumulator for the
+    # three TF32 products), 300 real signals (three 128-row blocks, odd count) and 70 complex
+    # ones (two 64-signal blocks); sampled rows against the FP64 oracle's fast projection
+    dev = _cuda()
+    N, W, eps = 32768, 0.25, 1e-14
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    # at eps = 1e-14 an eigenvalue within rounding of the 1 - eps threshold may fall on either
+    # side in the two FP64 solvers; such a vector has |D| ~ eps and moves the result by ~1e-14
+    assert p.r > 64 and abs(p.r - o.r) <= 1
+    g = np.random.default_rng(21)
+    yr = torch.from_numpy(g.standard_normal((301, N))).float()
+    yc = torch.complex(torch.from_numpy(g.standard_normal((70, N))).float(),
+                       torch.from_numpy(g.standard_normal((70, N))).float())
+    outr = p.project(yr.to(dev)).cpu().numpy()
+    outc = p.project(yc.to(dev)).cpu().numpy()
+    for y, out, rows in ((yr, outr, [0, 1, 127, 128, 255, 256, 300]), (yc, outc, [0, 63, 64, 69])):
+        ys = y[rows].numpy().astype(np.complex128 if y.is_complex() else np.float64)
+        fast = O.fast_project(o, ys.T).T
+        assert np.all(rel_err(out[rows], fast, ys) < 1e-5)
+
+
 def test_apply_prolate_direct_sum():
     dev = _cuda()
     N, W = 2049, 0.21
