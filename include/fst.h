@@ -114,11 +114,18 @@ fst_status fst_plan_export(fst_plan_t plan, int64_t *idx, double *lam, double *D
  * (Section 1.3, "Fast projections onto the range of S_K").
  *   y, out  device pointers, `batch` signals each, stride ld (0 = N).  y and out
  *           may be equal (in place); otherwise they must not overlap.
- *   dtype   FST_F32 / FST_C64: FP32 FFT convolution and FP32 correction;
+ *   dtype   FST_F32 / FST_C64: FP32 FFT convolution and FP32-accurate correction;
  *           FST_F64 / FST_C128: the same kernels in FP64.
  * Real signals are processed two at a time as the real and imaginary parts of
  * one complex FFT (B and S_T are real, so they do not mix).
+ * FP32: when y is 16-byte aligned and its row stride is a multiple of 16 bytes,
+ * S_T^T y for the whole batch runs on the tensor cores (TF32 with a hi/lo split,
+ * three products); other layouts use another kernel with another summation order
+ * (same accuracy).  Results are bit-for-bit repeatable for the same call.
  * Errors: FST_EINVAL (NULL pointer, batch < 0, ld < N), FST_ENOMEM, FST_ECUDA.
+ * The call is asynchronous: should a device-side wait of the tensor-core kernel
+ * run past its time limit, that launch gives up and the affected outputs are NaN
+ * (no status code can report it).
  * batch == 0 is a no-op returning FST_OK.
  */
 fst_status fst_project(fst_plan_t plan, const void *y, void *out, int64_t batch,
