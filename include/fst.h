@@ -173,6 +173,22 @@ fst_status fst_coeffs(fst_plan_t plan, const void *y, void *coeffs, int64_t batc
                       int dtype, void *stream);
 
 /*
+ * fst_expand -- T1 c for `batch` coefficient vectors: the expansion side of the fast
+ * factorization S_K S_K^* ~ T1 T2^* (Section 1.3; T1 = [F_{N,W}  L1  U1] with L1 from the
+ * constructive proof of Theorem 1, Section 2, and U1 from Corollary 2), so that
+ * fst_expand(fst_coeffs(y)) approximates S_K S_K^T y within 2 eps ||y||.
+ *   coeffs  device pointer, batch x K' complex (the layout fst_coeffs writes).
+ *   out     device pointer, batch x N complex, contiguous (for real signals the
+ *           imaginary part is the approximation's residue, of order eps).
+ *   dtype   FST_C64 (FP32 kernels) or FST_C128 (FP64 kernels).
+ * Uses the plan's workspace (grown on demand).
+ * Errors: FST_EINVAL (NULL, batch < 0, real dtype, non-projection plan),
+ * FST_EUNSUPPORTED (N not a power of two), FST_ENOMEM, FST_ECUDA.
+ */
+fst_status fst_expand(fst_plan_t plan, const void *coeffs, void *out, int64_t batch, int dtype,
+                      void *stream);
+
+/*
  * fst_coeffs_info -- sizes of the coefficient vector (any pointer may be NULL):
  * K' = 2NW' + r1 + r, nF = 2NW', r1 = 4 r_H + 4 r_A + 2 (2 r_B - 1) and the ranks
  * r_H, r_A, r_B of Section 2.  Builds the construction's tables on first use.

@@ -14,6 +14,14 @@
 //           n-chunk); the reduce kernel adds the chunks in a fixed order and applies
 //           C_A, C_B.
 //   U2^* y: sqrt|D_l| s_l^T y (partials per n-chunk, then a fixed-order reduce).
+//
+// and of its expansion T1 c (fst_expand), T1 = [F_{N,W}  L1  U1]:
+//   F c_F : the bins scattered (conjugated) into a length-N row, the library's forward DFT,
+//           conjugated and divided by sqrt(N) (= the inverse DFT restricted to -h..h).
+//   L1 c_L: per sample, the same generated columns as above (ADI Z and J Z, centred monomials,
+//           phase ramps D_A, D_B) summed against the eight coefficient blocks; no reduction
+//           across samples.
+//   U1 c_U: sum_l sign(D_l) sqrt|D_l| s_l c_U[l].
 #pragma once
 #include "fst_kernels.cuh"
 
@@ -336,6 +344,91 @@ FST_HD c2<T> coef_mix_value(const CoefArgs<T> &a, const T *raw, const T *rawU, c
     return mk<T>(a.acoefU[((sig / 2) * 2 + (sig & 1)) * a.rpad + j], (T)0);
   }
   return mk<T>(sqrtD[j] * rawU[2 * j], sqrtD[j] * rawU[2 * j + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// T1 c (fst_expand)
+// ---------------------------------------------------------------------------
+template <typename T> struct ExpArgs {
+  const c2<T> *coef;    // [batch][Kp]: F bins k = -h..h, L blocks b1..b8, U part
+  int64_t Kp, h, N;
+  int rH, DA, DB, r, rpad;
+  const T *zfirst, *zshift;   // ADI recurrence factors (as CoefArgs)
+  const c2<T> *phA, *phB;     // exp(-j 2 pi W' n) = conj(D_A), exp(-j pi (W + W') n) = conj(D_B)
+  const T *ST;                // [N][rpad]
+  const T *D, *sqrtD;         // [r]
+  const c2<T> *X;             // forward DFT of the launch group's scattered rows, layout Lf
+  Layout Lf;
+  int64_t sig0;               // first signal of the launch group
+  c2<T> *out;                 // [batch][N]
+};
+
+// row sl of the launch group: Xs[n] = conj(c_F[k]) at the bin k = n (n <= h) or n - N
+// (n >= N - h), zero elsewhere (2h + 1 <= N, so the two ranges do not meet)
+template <typename T> FST_HD void exp_scatter_body(const ExpArgs<T> &a, int64_t sl, int64_t n, c2<T> *Xs) {
+  const int64_t k = (n <= a.h) ? n : n - a.N;
+  c2<T> v = mk<T>(0, 0);
+  if (k >= -a.h && k <= a.h) v = cconj(a.coef[(a.sig0 + sl) * a.Kp + (k + a.h)]);
+  Xs[sl * a.N + n] = v;
+}
+
+// (T1 c)[n] of signal sig0 + sl
+template <typename T> FST_HD void exp_sample_body(const ExpArgs<T> &a, int64_t sl, int64_t n) {
+  const int64_t sig = a.sig0 + sl;
+  const c2<T> *b1 = a.coef + sig * a.Kp + (2 * a.h + 1);
+  const c2<T> *b2 = b1 + a.rH, *b3 = b2 + a.rH, *b4 = b3 + a.rH, *b5 = b4 + a.rH;
+  const c2<T> *b6 = b5 + a.DA, *b7 = b6 + a.DA, *b8 = b7 + a.DB, *cu = b8 + a.DB;
+  // Z_k at x = n + 1/2 and at N - x (J Z), by the recurrence of the coefficient kernels
+  const T x = (T)n + (T)0.5, xr = (T)a.N - x;
+  T zf = coef_div(a.zfirst[0], x + a.zshift[0]);
+  T zr = coef_div(a.zfirst[0], xr + a.zshift[0]);
+  c2<T> s1 = mk<T>(0, 0), s2 = s1, s3 = s1, s4 = s1;
+  for (int k = 0; k < a.rH; ++k) {
+    if (k > 0) {
+      const T pk = a.zshift[k], pk1 = a.zshift[k - 1], sc = a.zfirst[k];
+      zf = coef_div(sc * (x - pk1) * zf, x + pk);
+      zr = coef_div(sc * (xr - pk1) * zr, xr + pk);
+    }
+    s1 = cadd(s1, cscale(b1[k], zf));
+    s2 = cadd(s2, cscale(b2[k], zr));
+    s3 = cadd(s3, cscale(b3[k], zf));
+    s4 = cadd(s4, cscale(b4[k], zr));
+  }
+  // centred monomials u^i, u = (n - (N - 1)/2) / N
+  const T u = ((T)n - (T)(0.5 * (double)(a.N - 1))) * (T)(1.0 / (double)a.N);
+  c2<T> m5 = mk<T>(0, 0), m6 = m5, m7 = m5, m8 = m5;
+  T up = 1;
+  const int D = a.DA > a.DB ? a.DA : a.DB;
+  for (int i = 0; i < D; ++i) {
+    if (i < a.DA) {
+      m5 = cadd(m5, cscale(b5[i], up));
+      m6 = cadd(m6, cscale(b6[i], up));
+    }
+    if (i < a.DB) {
+      m7 = cadd(m7, cscale(b7[i], up));
+      m8 = cadd(m8, cscale(b8[i], up));
+    }
+    up *= u;
+  }
+  // L1 c_L = D_A (c (s1 - s2) + m5 / 2j) + D_A^* (c (s4 - s3) - m6 / 2j) + D_B m7 / 2 + D_B^* m8 / 2,
+  // c = 1 / (2 j pi) = -j / (2 pi), 1 / 2j = -j / 2
+  const T ip = (T)0.15915494309189533577;   // 1 / (2 pi)
+  const c2<T> dA = cconj(a.phA[n]), dB = cconj(a.phB[n]);
+  const c2<T> d12 = csub(s1, s2), d43 = csub(s4, s3);
+  const c2<T> tA = mk<T>(ip * d12.y + (T)0.5 * m5.y, -ip * d12.x - (T)0.5 * m5.x);
+  const c2<T> tC = mk<T>(ip * d43.y - (T)0.5 * m6.y, -ip * d43.x + (T)0.5 * m6.x);
+  c2<T> v = cadd(cmul(dA, tA), cmul(cconj(dA), tC));
+  v = cadd(v, cadd(cmul(dB, cscale(m7, (T)0.5)), cmul(cconj(dB), cscale(m8, (T)0.5))));
+  // U1 c_U
+  const T *srow = a.ST + n * a.rpad;
+  for (int j = 0; j < a.r; ++j) {
+    const T w = srow[j] * (a.D[j] < 0 ? -a.sqrtD[j] : a.sqrtD[j]);
+    v = cadd(v, cscale(cu[j], w));
+  }
+  // F c_F = conj(DFT_N(conj of the scattered bins)) / sqrt(N)
+  const c2<T> xf = a.X[sl * a.N + spec_pos(a.Lf, n)];
+  v = cadd(v, cscale(cconj(xf), (T)(1.0 / sqrt((double)a.N))));
+  a.out[sig * a.N + n] = v;
 }
 
 }  // namespace fst

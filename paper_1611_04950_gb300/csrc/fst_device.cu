@@ -202,6 +202,18 @@ __global__ void k_gather(const double *S, int64_t N, const int *sel, int r, int 
   }
 }
 
+// ---- T1 c (fst_expand) ----
+template <typename T> __global__ void k_exp_scatter(const ExpArgs<T> a, int64_t nsig, c2<T> *Xs) {
+  const int64_t total = nsig * a.N;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    exp_scatter_body<T>(a, t / a.N, t % a.N, Xs);
+}
+template <typename T> __global__ void k_expand(const ExpArgs<T> a, int64_t nsig) {
+  const int64_t total = nsig * a.N;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    exp_sample_body<T>(a, t / a.N, t % a.N);
+}
+
 // ---- fast coefficient vector kernels ----
 template <typename T> __global__ void __launch_bounds__(COEF_THREADS) k_coef_lowrank(const CoefArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -758,6 +770,20 @@ struct DevRunner : Runner {
     LAUNCHED("k_coef_mix");
     return FST_OK;
   }
+  template <typename T> fst_status exp_scatter_t(const ExpArgs<T> &a, int64_t nsig, c2<T> *Xs) {
+    PROF("k_exp_scatter", nsig, (k_exp_scatter<T><<<grid_for(nsig * a.N, 256), 256, 0, cur>>>(a, nsig, Xs)));
+    LAUNCHED("k_exp_scatter");
+    return FST_OK;
+  }
+  template <typename T> fst_status expand_t(const ExpArgs<T> &a, int64_t nsig) {
+    PROF("k_expand", nsig, (k_expand<T><<<grid_for(nsig * a.N, 256), 256, 0, cur>>>(a, nsig)));
+    LAUNCHED("k_expand");
+    return FST_OK;
+  }
+  fst_status exp_scatter(const ExpArgs<float> &a, int64_t nsig, float2 *Xs) override { return exp_scatter_t(a, nsig, Xs); }
+  fst_status exp_scatter(const ExpArgs<double> &a, int64_t nsig, double2 *Xs) override { return exp_scatter_t(a, nsig, Xs); }
+  fst_status expand(const ExpArgs<float> &a, int64_t nsig) override { return expand_t(a, nsig); }
+  fst_status expand(const ExpArgs<double> &a, int64_t nsig) override { return expand_t(a, nsig); }
   fst_status coef_lowrank(const CoefArgs<float> &a) override { return coef_lowrank_t(a); }
   fst_status coef_lowrank(const CoefArgs<double> &a) override { return coef_lowrank_t(a); }
   fst_status coef_st(const CoefArgs<float> &a) override { return coef_st_t(a); }

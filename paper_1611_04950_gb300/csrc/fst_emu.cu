@@ -223,6 +223,20 @@ struct EmuRunner : Runner {
       }
     return FST_OK;
   }
+  template <typename T> fst_status exp_scatter_t(const ExpArgs<T> &a, int64_t nsig, c2<T> *Xs) {
+    for (int64_t s = 0; s < nsig; ++s)
+      for (int64_t n = 0; n < a.N; ++n) exp_scatter_body<T>(a, s, n, Xs);
+    return FST_OK;
+  }
+  template <typename T> fst_status expand_t(const ExpArgs<T> &a, int64_t nsig) {
+    for (int64_t s = 0; s < nsig; ++s)
+      for (int64_t n = 0; n < a.N; ++n) exp_sample_body<T>(a, s, n);
+    return FST_OK;
+  }
+  fst_status exp_scatter(const ExpArgs<float> &a, int64_t nsig, float2 *Xs) override { return exp_scatter_t(a, nsig, Xs); }
+  fst_status exp_scatter(const ExpArgs<double> &a, int64_t nsig, double2 *Xs) override { return exp_scatter_t(a, nsig, Xs); }
+  fst_status expand(const ExpArgs<float> &a, int64_t nsig) override { return expand_t(a, nsig); }
+  fst_status expand(const ExpArgs<double> &a, int64_t nsig) override { return expand_t(a, nsig); }
   template <typename T> fst_status coef_st_t(const CoefArgs<T> &a) {
     std::vector<T> red((COEF_THREADS / 32) * 128);
     for (int64_t sig = 0; sig < a.batch; ++sig)

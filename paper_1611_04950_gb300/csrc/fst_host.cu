@@ -1205,6 +1205,92 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
   return FST_OK;
 }
 
+// T1 c for `batch` coefficient vectors (Section 1.3, the fast factorization S_K S_K^* ~ T1 T2^*):
+// per launch group of signals, the F bins are scattered and transformed by the forward DFT,
+// then one pass over the samples adds the L1 and U1 parts
+template <typename T> struct ExpPtrs;
+template <> struct ExpPtrs<float> {
+  static void fill(fst_plan_t p, ExpArgs<float> &e) {
+    const CoefPlan *c = p->coef;
+    e.zfirst = c->zfirst32; e.zshift = c->zshift32; e.phA = c->phA32; e.phB = c->phB32;
+    e.ST = p->ST32; e.D = p->D32; e.sqrtD = c->sqrtD32;
+  }
+};
+template <> struct ExpPtrs<double> {
+  static void fill(fst_plan_t p, ExpArgs<double> &e) {
+    const CoefPlan *c = p->coef;
+    e.zfirst = c->zfirst64; e.zshift = c->zshift64; e.phA = c->phA64; e.phB = c->phB64;
+    e.ST = p->ST64; e.D = p->D64; e.sqrtD = c->sqrtD64;
+  }
+};
+
+template <typename T>
+static fst_status expand_t(fst_plan_t p, const c2<T> *coef, c2<T> *out, int64_t batch) {
+  using C = c2<T>;
+  Runner *R = p->R;
+  TRY(build_coef(p));
+  const CoefPlan *cp = p->coef;
+  const int64_t N = p->N;
+  const bool dbl = sizeof(T) == 8;
+  int log2N = 0;
+  while ((1LL << log2N) < N) ++log2N;
+  Layout Lf = make_layout(N, log2N, dbl, 0, false);
+  if (!Lf.small) Lf.Pnz = 1 << Lf.log2P;
+  // scratch: the scattered rows of one launch group, then the forward transform's own
+  const size_t xs_b = ((size_t)Lf.chunk * N * sizeof(C) + 255) / 256 * 256;
+  TRY(ensure_ws(p, xs_b + ws_need(Lf, dbl, 0, true) + 4096));
+  C *Xs = (C *)p->ws;
+  char *wf = (char *)p->ws + xs_b;
+  ExpArgs<T> e{};
+  e.coef = coef;
+  e.Kp = cp->odd + cp->r1 + p->r;
+  e.h = cp->h;
+  e.N = N;
+  e.rH = cp->rH;
+  e.DA = cp->DA;
+  e.DB = cp->DB;
+  e.r = (int)p->r;
+  e.rpad = (int)p->rpad;
+  ExpPtrs<T>::fill(p, e);
+  e.Lf = Lf;
+  e.out = out;
+  ConvArgs<T> a{};
+  a.y = (const T *)Xs;
+  a.ld = N;
+  a.cplx = 1;
+  a.N = N;
+  a.tw = plan_tw<T>(p);
+  a.mode = MODE_FORWARD;
+  a.log2M = Lf.log2M;
+  a.log2P = Lf.log2P;
+  a.log2Q = Lf.log2Q;
+  a.Pnz = Lf.Pnz;
+  a.NB = Lf.NB;
+  a.G = Lf.G;
+  a.inter = (C *)wf;
+  if (!Lf.small) {
+    a.part = (T *)(wf + (size_t)Lf.chunk * N * sizeof(C));
+    a.acoef = a.part;
+  }
+  for (int64_t s0 = 0; s0 < batch; s0 += Lf.chunk) {
+    const int64_t nsig = std::min<int64_t>(Lf.chunk, batch - s0);
+    e.sig0 = s0;
+    TRY(R->exp_scatter(e, nsig, Xs));
+    a.batch = nsig;
+    a.pair0 = 0;
+    a.npairs = nsig;
+    if (Lf.small) {
+      TRY(R->small(a, Lf));
+    } else {
+      TRY(R->passA(a, Lf));
+      TRY(R->passB(a, Lf));
+    }
+    e.X = (const C *)a.inter;
+    TRY(R->expand(e, nsig));
+  }
+  return FST_OK;
+}
+
 static fst_status run_coeffs(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld, int dtype) {
   if (!p) return fail(FST_EINVAL, "plan is NULL");
   if (batch < 0) return fail(FST_EINVAL, "batch < 0");
@@ -1232,6 +1318,21 @@ fst_status fst_coeffs(fst_plan_t p, const void *y, void *coeffs, int64_t batch, 
   if (!p) return fail(FST_EINVAL, "plan is NULL");
   p->R->set_stream(stream);
   return run_coeffs(p, y, coeffs, batch, ld, dtype);
+}
+
+fst_status fst_expand(fst_plan_t p, const void *coeffs, void *out, int64_t batch, int dtype, void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FST_EINVAL, "batch < 0");
+  if (batch == 0) return FST_OK;
+  if (!coeffs || !out) return fail(FST_EINVAL, "NULL pointer");
+  if (p->op != FST_OP_PROJECT) return fail(FST_EINVAL, "expansion needs a projection plan");
+  if ((p->N & (p->N - 1)) != 0) return fail(FST_EUNSUPPORTED, "expansion needs N a power of two");
+  p->R->set_stream(stream);
+  switch (dtype) {
+    case FST_C64: return fst::expand_t<float>(p, (const float2 *)coeffs, (float2 *)out, batch);
+    case FST_C128: return fst::expand_t<double>(p, (const double2 *)coeffs, (double2 *)out, batch);
+    default: return fail(FST_EINVAL, "coefficients are complex: dtype FST_C64 or FST_C128");
+  }
 }
 
 fst_status fst_coeffs_info(fst_plan_t p, int64_t *Kprime, int64_t *nF, int64_t *r1, int64_t *rH, int64_t *rA,

@@ -72,6 +72,11 @@ struct Runner {
   virtual int sm_count() const { return 1; }
   virtual fst_status corr_reduce(const ConvArgs<float> &a, const float *scale) { return FST_EUNSUPPORTED; }
   virtual fst_status corr_z(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  // T1 c (fst_expand): scatter of the F bins of nsig signals into Xs, then the samples
+  virtual fst_status exp_scatter(const ExpArgs<float> &a, int64_t nsig, float2 *Xs) = 0;
+  virtual fst_status exp_scatter(const ExpArgs<double> &a, int64_t nsig, double2 *Xs) = 0;
+  virtual fst_status expand(const ExpArgs<float> &a, int64_t nsig) = 0;
+  virtual fst_status expand(const ExpArgs<double> &a, int64_t nsig) = 0;
   // out += S_T a on CUDA cores (FP32, r <= 64)
   virtual fst_status z_rmw(const ConvArgs<float> &a, const float *ST) { return FST_EUNSUPPORTED; }
 

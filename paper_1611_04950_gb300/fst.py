@@ -34,7 +34,7 @@ EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_
             "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
             "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
             "fst_project_noalloc", "fst_noalloc_scratch_bytes", "fst_coeffs", "fst_coeffs_info",
-            "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged"]
+            "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged", "fst_expand"]
 
 
 class FSTError(RuntimeError):
@@ -66,6 +66,7 @@ def _load():
         "fst_project_noalloc": ([P, vp, vp, i64, i64, I, vp], I),
         "fst_coeffs": ([P, vp, vp, i64, i64, I, vp], I),
         "fst_coeffs_info": ([P] + [C.POINTER(i64)] * 6, I),
+        "fst_expand": ([P, vp, vp, i64, I, vp], I),
         "fst_adi_shifts": ([i64, I, C.POINTER(d)], I),
         "fst_plan_many": ([C.POINTER(P), i64, C.POINTER(i64), C.POINTER(d), C.POINTER(i64), C.POINTER(d), vp], I),
         "fst_emu_plan_many": ([C.POINTER(P), i64, C.POINTER(i64), C.POINTER(d), C.POINTER(i64), C.POINTER(d)], I),
@@ -167,6 +168,10 @@ def fst_noalloc_scratch_bytes() -> int:
 def fst_coeffs(h: int, y_ptr: int, out_ptr: int, batch: int, ld: int, dtype: int, stream: int = 0):
     _check(_lib.fst_coeffs(C.c_void_p(h), C.c_void_p(y_ptr), C.c_void_p(out_ptr), batch, ld, dtype,
                            C.c_void_p(stream)))
+
+
+def fst_expand(h: int, c_ptr: int, out_ptr: int, batch: int, dtype: int, stream: int = 0):
+    _check(_lib.fst_expand(C.c_void_p(h), C.c_void_p(c_ptr), C.c_void_p(out_ptr), batch, dtype, C.c_void_p(stream)))
 
 
 def fst_coeffs_info(h: int) -> dict:
@@ -373,6 +378,23 @@ class Plan:
         out = torch.zeros((y.shape[0], Kp), dtype=ct, device=y.device)
         ld = y.stride(0) if y.shape[0] > 1 else self.N
         fst_coeffs(self.h, y.data_ptr(), out.data_ptr(), y.shape[0], ld, _dtype_code(y.dtype), _stream_handle(stream))
+        return out
+
+    def expand(self, c, stream=None):
+        """T1 c for a (batch, K') complex coefficient array: (batch, N) complex (Section 1.3)."""
+        if self.emulated:
+            c = np.ascontiguousarray(np.asarray(c))
+            if c.ndim == 1:
+                c = c[None]
+            out = np.zeros((c.shape[0], self.N), c.dtype)
+            fst_expand(self.h, c.ctypes.data, out.ctypes.data, c.shape[0], _dtype_code(c.dtype), 0)
+            return out
+        import torch
+        if c.dim() == 1:
+            c = c.unsqueeze(0)
+        c = c.contiguous()
+        out = torch.zeros((c.shape[0], self.N), dtype=c.dtype, device=c.device)
+        fst_expand(self.h, c.data_ptr(), out.data_ptr(), c.shape[0], _dtype_code(c.dtype), _stream_handle(stream))
         return out
 
     def project_host(self, y, out=None, stream=None):

@@ -231,6 +231,58 @@ def test_emulated_coeffs_expand_to_projection():
     assert np.linalg.norm(back - O.exact_project(N, W, p.K, y)) <= 2 * eps * np.linalg.norm(y)
 
 
+@pytest.mark.parametrize("N,W,eps", [(256, 0.2, 1e-6), (1024, 1 / 16, 1e-8)])
+def test_emulated_expand_matches_dense_T1(N, W, eps):
+    # T1 c of the library (matrix-free, emulated kernels) against the oracle's dense
+    # T1 = [F  L1  U1] on random complex coefficient vectors
+    from oracle import thm1 as T
+    p = P.Plan(N, W, eps=eps, emulate=True)
+    t = T.thm1(N, W, eps)
+    op = O.make_plan(N, W, None, eps)
+    Kp = F.fst_coeffs_info(p.h)["Kprime"]
+    rng = np.random.default_rng(N + 1)
+    c = rng.standard_normal((2, Kp)) + 1j * rng.standard_normal((2, Kp))
+    ref = np.stack([T.expand(t, op, ci) for ci in c])
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(p.expand(c) - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(p.expand(c.astype(np.complex64)) - ref)) <= 2e-5 * scale
+
+
+def test_emulated_expand_of_coeffs_is_the_projection():
+    # T1 T2^* y is within 2 eps ||y|| of S_K S_K^T y (Section 1.3), through both entry points
+    N, W, eps = 512, 0.2, 1e-6
+    p = P.Plan(N, W, eps=eps, emulate=True)
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((2, N))
+    exact = O.exact_project(N, W, p.K, y.T).T
+    back = p.expand(p.coeffs(y))
+    nrm = np.linalg.norm(y, axis=1)
+    assert np.all(np.linalg.norm(back - exact, axis=1) <= 2 * eps * nrm)
+    back32 = p.expand(p.coeffs(y.astype(np.float32)))
+    assert np.all(np.linalg.norm(back32 - exact, axis=1) <= 2 * eps * nrm + 1e-5 * nrm)
+    yc = y + 1j * rng.standard_normal((2, N))
+    exc = O.exact_project(N, W, p.K, yc.T).T
+    assert np.all(np.linalg.norm(p.expand(p.coeffs(yc)) - exc, axis=1) <= 2 * eps * np.linalg.norm(yc, axis=1))
+
+
+def test_expand_argument_errors():
+    p = P.Plan(128, 0.1, eps=1e-6, emulate=True)
+    Kp = F.fst_coeffs_info(p.h)["Kprime"]
+    c = np.zeros((1, Kp), np.complex128)
+    out = np.zeros((1, 128), np.complex128)
+    with pytest.raises(F.FSTError) as ei:
+        F.fst_expand(p.h, c.ctypes.data, out.ctypes.data, 1, F.FST_F64)
+    assert ei.value.status == F.FST_EINVAL
+    with pytest.raises(F.FSTError) as ei:
+        F.fst_expand(p.h, 0, out.ctypes.data, 1, F.FST_C128)
+    assert ei.value.status == F.FST_EINVAL
+    F.fst_expand(p.h, c.ctypes.data, out.ctypes.data, 0, F.FST_C128)     # batch 0: no-op
+    q = P.Plan(100, 0.1, eps=1e-6, emulate=True)
+    with pytest.raises(F.FSTError) as ei:
+        q.expand(np.zeros((1, 10), np.complex128))
+    assert ei.value.status == F.FST_EUNSUPPORTED
+
+
 def test_coeffs_need_power_of_two_and_projection():
     p = P.Plan(100, 0.1, eps=1e-6, emulate=True)
     with pytest.raises(F.FSTError) as ei:

@@ -260,6 +260,47 @@ def test_coeffs_against_oracle(N, W, eps):
         assert np.linalg.norm(back - ex) <= (2 * eps + 1e-5) * nrm[0, 0]
 
 
+def test_expand_against_dense_T1_and_roundtrip():
+    # T1 c on the GPU (FP64 and FP32) against the oracle's dense T1 on random coefficients,
+    # and T1 T2^* y against the exact projection (within 2 eps of it, Section 1.3)
+    from oracle import thm1 as T
+    dev = _cuda()
+    N, W, eps = 4096, 1 / 16, 1e-6
+    p = F.Plan(N, W, eps=eps)
+    t = T.thm1(N, W, eps)
+    o = oplan(N, W, p.K, eps)
+    Kp = F.fst_coeffs_info(p.h)["Kprime"]
+    g = np.random.default_rng(8)
+    c = g.standard_normal((3, Kp)) + 1j * g.standard_normal((3, Kp))
+    ref = np.stack([T.expand(t, o, ci) for ci in c])
+    scale = np.abs(ref).max()
+    e128 = p.expand(torch.from_numpy(c).to(dev)).cpu().numpy()
+    e64 = p.expand(torch.from_numpy(c.astype(np.complex64)).to(dev)).cpu().numpy()
+    assert np.max(np.abs(e128 - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(e64 - ref)) <= 2e-5 * scale
+    y = workloads.gaussian(2, N, seed=22)
+    ex = O.exact_project(N, W, p.K, y.numpy().T).T
+    nrm = np.linalg.norm(y.numpy(), axis=1)
+    back64 = p.expand(p.coeffs(y.to(dev))).cpu().numpy()
+    back32 = p.expand(p.coeffs(y.float().to(dev))).cpu().numpy()
+    assert np.all(np.linalg.norm(back64 - ex, axis=1) <= 2 * eps * nrm)
+    assert np.all(np.linalg.norm(back32 - ex, axis=1) <= (2 * eps + 1e-5) * nrm)
+
+
+def test_expand_roundtrip_large_N():
+    # N = 65536, eps = 1e-8: T1 T2^* y against the oracle's fast projection (each within a
+    # few eps of S_K S_K^T y), FP32 end to end on the device
+    dev = _cuda()
+    N, W, eps = 65536, 0.25, 1e-8
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    y = workloads.gaussian(2, N, seed=23)
+    fast = O.fast_project(o, y.numpy().T).T
+    back = p.expand(p.coeffs(y.float().to(dev))).cpu().numpy()
+    nrm = np.linalg.norm(y.numpy(), axis=1)
+    assert np.all(np.linalg.norm(back - fast, axis=1) <= (3 * eps + 2e-5) * nrm)
+
+
 def test_coeffs_complex_input():
     from oracle import thm1 as T
     dev = _cuda()
