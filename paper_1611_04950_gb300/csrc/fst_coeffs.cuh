@@ -372,63 +372,96 @@ template <typename T> FST_HD void exp_scatter_body(const ExpArgs<T> &a, int64_t 
   Xs[sl * a.N + n] = v;
 }
 
-// (T1 c)[n] of signal sig0 + sl
-template <typename T> FST_HD void exp_sample_body(const ExpArgs<T> &a, int64_t sl, int64_t n) {
+// (T1 c)[n] of signal sig0 + sl for the EXP_E samples n = n0 + i stride (i < EXP_E, n < N):
+// every coefficient and table value is loaded once for all of them
+constexpr int EXP_E = 4;
+template <typename T> FST_HD void exp_samples_body(const ExpArgs<T> &a, int64_t sl, int64_t n0, int64_t stride) {
   const int64_t sig = a.sig0 + sl;
   const c2<T> *b1 = a.coef + sig * a.Kp + (2 * a.h + 1);
   const c2<T> *b2 = b1 + a.rH, *b3 = b2 + a.rH, *b4 = b3 + a.rH, *b5 = b4 + a.rH;
   const c2<T> *b6 = b5 + a.DA, *b7 = b6 + a.DA, *b8 = b7 + a.DB, *cu = b8 + a.DB;
+  int64_t n[EXP_E];
+  bool ok[EXP_E];
+#pragma unroll
+  for (int i = 0; i < EXP_E; ++i) {
+    n[i] = n0 + i * stride;
+    ok[i] = n[i] < a.N;
+    if (!ok[i]) n[i] = a.N - 1;   // computed, not stored
+  }
   // Z_k at x = n + 1/2 and at N - x (J Z), by the recurrence of the coefficient kernels
-  const T x = (T)n + (T)0.5, xr = (T)a.N - x;
-  T zf = coef_div(a.zfirst[0], x + a.zshift[0]);
-  T zr = coef_div(a.zfirst[0], xr + a.zshift[0]);
-  c2<T> s1 = mk<T>(0, 0), s2 = s1, s3 = s1, s4 = s1;
+  T x[EXP_E], xr[EXP_E], zf[EXP_E], zr[EXP_E];
+  c2<T> s1[EXP_E], s2[EXP_E], s3[EXP_E], s4[EXP_E];
+#pragma unroll
+  for (int i = 0; i < EXP_E; ++i) {
+    x[i] = (T)n[i] + (T)0.5;
+    xr[i] = (T)a.N - x[i];
+    zf[i] = coef_div(a.zfirst[0], x[i] + a.zshift[0]);
+    zr[i] = coef_div(a.zfirst[0], xr[i] + a.zshift[0]);
+    s1[i] = s2[i] = s3[i] = s4[i] = mk<T>(0, 0);
+  }
   for (int k = 0; k < a.rH; ++k) {
-    if (k > 0) {
-      const T pk = a.zshift[k], pk1 = a.zshift[k - 1], sc = a.zfirst[k];
-      zf = coef_div(sc * (x - pk1) * zf, x + pk);
-      zr = coef_div(sc * (xr - pk1) * zr, xr + pk);
+    const T pk = a.zshift[k], pk1 = k > 0 ? a.zshift[k - 1] : (T)0, sc = a.zfirst[k];
+    const c2<T> c1 = b1[k], c2v = b2[k], c3 = b3[k], c4 = b4[k];
+#pragma unroll
+    for (int i = 0; i < EXP_E; ++i) {
+      if (k > 0) {
+        zf[i] = coef_div(sc * (x[i] - pk1) * zf[i], x[i] + pk);
+        zr[i] = coef_div(sc * (xr[i] - pk1) * zr[i], xr[i] + pk);
+      }
+      s1[i] = cadd(s1[i], cscale(c1, zf[i]));
+      s2[i] = cadd(s2[i], cscale(c2v, zr[i]));
+      s3[i] = cadd(s3[i], cscale(c3, zf[i]));
+      s4[i] = cadd(s4[i], cscale(c4, zr[i]));
     }
-    s1 = cadd(s1, cscale(b1[k], zf));
-    s2 = cadd(s2, cscale(b2[k], zr));
-    s3 = cadd(s3, cscale(b3[k], zf));
-    s4 = cadd(s4, cscale(b4[k], zr));
   }
   // centred monomials u^i, u = (n - (N - 1)/2) / N
-  const T u = ((T)n - (T)(0.5 * (double)(a.N - 1))) * (T)(1.0 / (double)a.N);
-  c2<T> m5 = mk<T>(0, 0), m6 = m5, m7 = m5, m8 = m5;
-  T up = 1;
+  T u[EXP_E], up[EXP_E];
+  c2<T> m5[EXP_E], m6[EXP_E], m7[EXP_E], m8[EXP_E];
+#pragma unroll
+  for (int i = 0; i < EXP_E; ++i) {
+    u[i] = ((T)n[i] - (T)(0.5 * (double)(a.N - 1))) * (T)(1.0 / (double)a.N);
+    up[i] = 1;
+    m5[i] = m6[i] = m7[i] = m8[i] = mk<T>(0, 0);
+  }
   const int D = a.DA > a.DB ? a.DA : a.DB;
-  for (int i = 0; i < D; ++i) {
-    if (i < a.DA) {
-      m5 = cadd(m5, cscale(b5[i], up));
-      m6 = cadd(m6, cscale(b6[i], up));
+  for (int d = 0; d < D; ++d) {
+    const bool inA = d < a.DA, inB = d < a.DB;
+    const c2<T> c5 = inA ? b5[d] : mk<T>(0, 0), c6 = inA ? b6[d] : mk<T>(0, 0);
+    const c2<T> c7 = inB ? b7[d] : mk<T>(0, 0), c8 = inB ? b8[d] : mk<T>(0, 0);
+#pragma unroll
+    for (int i = 0; i < EXP_E; ++i) {
+      m5[i] = cadd(m5[i], cscale(c5, up[i]));
+      m6[i] = cadd(m6[i], cscale(c6, up[i]));
+      m7[i] = cadd(m7[i], cscale(c7, up[i]));
+      m8[i] = cadd(m8[i], cscale(c8, up[i]));
+      up[i] *= u[i];
     }
-    if (i < a.DB) {
-      m7 = cadd(m7, cscale(b7[i], up));
-      m8 = cadd(m8, cscale(b8[i], up));
-    }
-    up *= u;
+  }
+  // U1 c_U: weights sign(D) sqrt|D| c_U[j], applied to the S_T rows of the samples
+  c2<T> v[EXP_E];
+#pragma unroll
+  for (int i = 0; i < EXP_E; ++i) v[i] = mk<T>(0, 0);
+  for (int j = 0; j < a.r; ++j) {
+    const c2<T> w = cscale(cu[j], a.D[j] < 0 ? -a.sqrtD[j] : a.sqrtD[j]);
+#pragma unroll
+    for (int i = 0; i < EXP_E; ++i) v[i] = cadd(v[i], cscale(w, a.ST[n[i] * a.rpad + j]));
   }
   // L1 c_L = D_A (c (s1 - s2) + m5 / 2j) + D_A^* (c (s4 - s3) - m6 / 2j) + D_B m7 / 2 + D_B^* m8 / 2,
-  // c = 1 / (2 j pi) = -j / (2 pi), 1 / 2j = -j / 2
+  // c = 1 / (2 j pi) = -j / (2 pi), 1 / 2j = -j / 2; then F c_F = conj(DFT_N(conj bins)) / sqrt(N)
   const T ip = (T)0.15915494309189533577;   // 1 / (2 pi)
-  const c2<T> dA = cconj(a.phA[n]), dB = cconj(a.phB[n]);
-  const c2<T> d12 = csub(s1, s2), d43 = csub(s4, s3);
-  const c2<T> tA = mk<T>(ip * d12.y + (T)0.5 * m5.y, -ip * d12.x - (T)0.5 * m5.x);
-  const c2<T> tC = mk<T>(ip * d43.y - (T)0.5 * m6.y, -ip * d43.x + (T)0.5 * m6.x);
-  c2<T> v = cadd(cmul(dA, tA), cmul(cconj(dA), tC));
-  v = cadd(v, cadd(cmul(dB, cscale(m7, (T)0.5)), cmul(cconj(dB), cscale(m8, (T)0.5))));
-  // U1 c_U
-  const T *srow = a.ST + n * a.rpad;
-  for (int j = 0; j < a.r; ++j) {
-    const T w = srow[j] * (a.D[j] < 0 ? -a.sqrtD[j] : a.sqrtD[j]);
-    v = cadd(v, cscale(cu[j], w));
+  const T rs = (T)(1.0 / sqrt((double)a.N));
+#pragma unroll
+  for (int i = 0; i < EXP_E; ++i) {
+    if (!ok[i]) continue;
+    const c2<T> dA = cconj(a.phA[n[i]]), dB = cconj(a.phB[n[i]]);
+    const c2<T> d12 = csub(s1[i], s2[i]), d43 = csub(s4[i], s3[i]);
+    const c2<T> tA = mk<T>(ip * d12.y + (T)0.5 * m5[i].y, -ip * d12.x - (T)0.5 * m5[i].x);
+    const c2<T> tC = mk<T>(ip * d43.y - (T)0.5 * m6[i].y, -ip * d43.x + (T)0.5 * m6[i].x);
+    c2<T> r = cadd(v[i], cadd(cmul(dA, tA), cmul(cconj(dA), tC)));
+    r = cadd(r, cadd(cmul(dB, cscale(m7[i], (T)0.5)), cmul(cconj(dB), cscale(m8[i], (T)0.5))));
+    const c2<T> xf = a.X[sl * a.N + spec_pos(a.Lf, n[i])];
+    r = cadd(r, cscale(cconj(xf), rs));
+    a.out[sig * a.N + n[i]] = r;
   }
-  // F c_F = conj(DFT_N(conj of the scattered bins)) / sqrt(N)
-  const c2<T> xf = a.X[sl * a.N + spec_pos(a.Lf, n)];
-  v = cadd(v, cscale(cconj(xf), (T)(1.0 / sqrt((double)a.N))));
-  a.out[sig * a.N + n] = v;
 }
-
 }  // namespace fst

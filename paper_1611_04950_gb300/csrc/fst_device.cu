@@ -208,10 +208,11 @@ template <typename T> __global__ void k_exp_scatter(const ExpArgs<T> a, int64_t 
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
     exp_scatter_body<T>(a, t / a.N, t % a.N, Xs);
 }
-template <typename T> __global__ void k_expand(const ExpArgs<T> a, int64_t nsig) {
-  const int64_t total = nsig * a.N;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    exp_sample_body<T>(a, t / a.N, t % a.N);
+// block b of a signal row: samples b (EXP_E 256) + tid + i 256, i < EXP_E
+template <typename T> __global__ void __launch_bounds__(256) k_expand(const ExpArgs<T> a, int64_t nsig) {
+  const int64_t per = (a.N + EXP_E * 256 - 1) / (EXP_E * 256);
+  for (int64_t bb = blockIdx.x; bb < nsig * per; bb += gridDim.x)
+    exp_samples_body<T>(a, bb / per, (bb % per) * (EXP_E * 256) + threadIdx.x, 256);
 }
 
 // ---- fast coefficient vector kernels ----
@@ -776,7 +777,8 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status expand_t(const ExpArgs<T> &a, int64_t nsig) {
-    PROF("k_expand", nsig, (k_expand<T><<<grid_for(nsig * a.N, 256), 256, 0, cur>>>(a, nsig)));
+    const int64_t blocks = nsig * ((a.N + EXP_E * 256 - 1) / (EXP_E * 256));
+    PROF("k_expand", nsig, (k_expand<T><<<(unsigned)std::min<int64_t>(blocks, 152 * 64), 256, 0, cur>>>(a, nsig)));
     LAUNCHED("k_expand");
     return FST_OK;
   }

@@ -229,8 +229,10 @@ struct EmuRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status expand_t(const ExpArgs<T> &a, int64_t nsig) {
+    const int64_t blk = EXP_E * 256;
     for (int64_t s = 0; s < nsig; ++s)
-      for (int64_t n = 0; n < a.N; ++n) exp_sample_body<T>(a, s, n);
+      for (int64_t b0 = 0; b0 < a.N; b0 += blk)
+        for (int t = 0; t < 256; ++t) exp_samples_body<T>(a, s, b0 + t, 256);
     return FST_OK;
   }
   fst_status exp_scatter(const ExpArgs<float> &a, int64_t nsig, float2 *Xs) override { return exp_scatter_t(a, nsig, Xs); }
