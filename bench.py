@@ -64,6 +64,22 @@ def make_workload(name, device, batch=None):
     raise ValueError(name)
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (the whole job's time is the slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(samples_per_rank, world, seconds):
+    """Weak scaling: every rank projects its own batch; value = all ranks' samples / time."""
+    return samples_per_rank * world / seconds
+
+
 def ncu_traffic(kernel, pairs_per_launch):
     """DRAM bytes (read + write) of one launch of `kernel`, from the ncu capture summarised in
     profiles/ncu_traffic.txt (lines: kernel, bytes, pairs per captured launch), scaled to this
@@ -334,13 +350,9 @@ def main():
     barrier()
     launches = F.fst_launch_count() - l0
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     samples_per_step = B * N * world
-    value = samples_per_step / (ms * 1e-3)
+    value = job_throughput(B * N, world, ms * 1e-3)
 
     # per-kernel launch times (separate pass with events around every launch)
     F.fst_profile_enable(True)
@@ -424,12 +436,8 @@ def main():
         for _ in range(k2):
             e2e_step()
         torch.cuda.synchronize()
-        wall = (time.perf_counter() - t0) / k2
-        if world > 1:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": samples_per_step / wall, "unit": "samples/s", "h2d_bytes_per_step": nbytes_in,
+        wall = max_over_ranks((time.perf_counter() - t0) / k2, world, "cuda")
+        e2e = {"value": job_throughput(B * N, world, wall), "unit": "samples/s", "h2d_bytes_per_step": nbytes_in,
                "d2h_bytes_per_step": nbytes_out, "ms_per_step": wall * 1e3}
 
     cpu = None
