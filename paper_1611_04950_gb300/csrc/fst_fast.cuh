@@ -499,9 +499,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
 namespace fst {
 
 // ---------------------------------------------------------------------------
-// Standalone rank-r correction for the FP32 four-step path with P > 32 (and any
-// layout without the register column passes): the same tensor-core products as the
-// fast column kernels, on contiguous row blocks of CORR_ROWS samples:
+// Standalone rank-r correction with mma.sync, for FP32 batches whose signal rows no TMA
+// tensor map can address (otherwise the tcgen05 kernel computes S_T^T y): the same
+// tensor-core products as the fast column kernels, on contiguous row blocks of CORR_ROWS
+// samples:
 //   k_corr_c : partial S_T^T y per (pair group, row block)   (before pass C)
 //   k_corr_z : out += S_T (D o c) per (pair group, row block) (after pass C)
 // ---------------------------------------------------------------------------

@@ -164,7 +164,7 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   const size_t slot = slot_bytes(L, sizeof(T) == 8, a.rpad, a.mode == MODE_FORWARD);
   // separate correction (FP32 device): a = D o S_T^T y over every pair first (before any
   // output is written, so y == out works); on tcgen05 whenever the signal rows allow a
-  // tensor map, else mma.sync kernels for P > 32.  Then out += S_T a: in the fast column
+  // tensor map, else (P > 32) mma.sync kernels.  Then out += S_T a: in the fast column
   // pass C, or by a last kernel over the whole batch.
   const bool want = a.mode == MODE_FULL && a.r > 0 && sizeof(T) == 4 && R->device() && !L.small;
   const bool tc = want && tc_usable(*reinterpret_cast<const ConvArgs<float> *>(&a));

@@ -45,7 +45,7 @@ struct Layout {
   bool small = true;
   bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
   bool fused_reduce = false;  // the row pass also sums the correction partials (device fast path, Q = 4096)
-  bool split_corr = false;    // correction as separate row-block kernels (device FP32 four-step, P > 32)
+  bool split_corr = false;    // correction outside the column passes (device FP32 four-step, P > 32)
   int log2M = 0, log2P = 0, log2Q = 0;
   int Pnz = 0, NB = 0, G = 1, ntiles = 0;
   int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
