@@ -265,6 +265,30 @@ def test_emulated_expand_of_coeffs_is_the_projection():
     assert np.all(np.linalg.norm(p.expand(p.coeffs(yc)) - exc, axis=1) <= 2 * eps * np.linalg.norm(yc, axis=1))
 
 
+def test_emulated_coeffs_and_expand_across_launch_groups(monkeypatch):
+    # 1 MiB launch groups of 8 (N = 8192, FP64): 18 real signals are 9 pairs, two groups for the
+    # coefficients, and 18 coefficient rows, three groups for the expansion; rows from every group
+    # against the oracle
+    from oracle import thm1 as T
+    monkeypatch.setenv("FST_CHUNK_MB", "1")
+    N, W, eps = 8192, 1 / 16, 1e-6
+    p = P.Plan(N, W, eps=eps, emulate=True)
+    t = T.thm1(N, W, eps)
+    op = O.make_plan(N, W, None, eps)
+    rng = np.random.default_rng(11)
+    y = rng.standard_normal((18, N))
+    c = p.coeffs(y)
+    rows = [0, 15, 16, 17]
+    ref = T.coeffs(t, op, y[rows].T).T
+    nrm = np.linalg.norm(y[rows], axis=1)[:, None]
+    # FP64 rounding of the ADI column sums grows with N: ~2e-12 ||y|| at N = 8192 (the GPU FP64
+    # coefficient test uses the same 1e-11 bound)
+    assert np.all(np.abs(c[rows] - ref) <= 1e-11 * nrm)
+    back = p.expand(c)
+    dense = np.stack([T.expand(t, op, c[i]) for i in rows])
+    assert np.max(np.abs(back[rows] - dense)) <= 1e-11 * np.abs(dense).max()
+
+
 def test_expand_argument_errors():
     p = P.Plan(128, 0.1, eps=1e-6, emulate=True)
     Kp = F.fst_coeffs_info(p.h)["Kprime"]
