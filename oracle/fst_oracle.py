@@ -13,7 +13,7 @@ Notation: N signal length, W half-bandwidth in (0, 1/2), K number of Slepian
 vectors kept, eps tolerance, M FFT length, B the prolate matrix, S_{N,W} the
 Slepian basis (columns s^(l), eigenvalues lambda_l in descending order).
 
-Readings taken where the paper is silent (each one is listed in the design doc):
+Readings taken where the paper is silent:
   * The commuting tridiagonal matrix used to compute the DPSS is Slepian's (1978),
     which the paper cites for the DPSS but does not write out (Section 1.1).
   * "log" in every bound is the natural logarithm.
@@ -336,9 +336,3 @@ def exact_project(N: int, W: float, K: int, y: np.ndarray) -> np.ndarray:
         return SK @ (SK.T @ y)
     ref = make_plan(N, W, K, EPS_REF)
     return fast_project(ref, y)
-
-
-def exact_coefficients(N: int, W: float, K: int, y: np.ndarray) -> np.ndarray:
-    """S_K^* y with the sign convention of dpss_window (tiny N only)."""
-    S = dpss_window(N, W, 0, K - 1)
-    return S.T @ y

@@ -12,7 +12,7 @@ check and the benchmark's CPU leg use it.
 The coefficient vector of a signal y is T2^* y = [F^* y; L2^* y; U2^* y] (length
 K' = 2NW' + r1 + r2), and T1 (T2^* y) is within 2 eps ||y|| of S_K S_K^* y.
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
   * "2NW' is the nearest odd integer to W" is read as nearest odd integer to 2NW;
     ties (2NW an even integer) round up: 2NW' = 2 floor(NW) + 1.
   * D_B[n,n] = exp(j pi (W + W') n): the pi is needed for the cosine identity
