@@ -122,10 +122,16 @@ fst_status fst_plan_export(fst_plan_t plan, int64_t *idx, double *lam, double *D
  * S_T^T y for the whole batch runs on the tensor cores (TF32 with a hi/lo split,
  * three products); other layouts use another kernel with another summation order
  * (same accuracy).  Results are bit-for-bit repeatable for the same call.
- * Errors: FST_EINVAL (NULL pointer, batch < 0, ld < N), FST_ENOMEM, FST_ECUDA.
- * The call is asynchronous: should a device-side wait of the tensor-core kernel
- * run past its time limit, that launch gives up and the affected outputs are NaN
- * (no status code can report it).
+ * Errors: FST_EINVAL (NULL pointer, batch < 0, ld < N), FST_ENOMEM, FST_ECUDA,
+ * FST_ETIMEOUT (see below).
+ * Device waits: every wait of the tensor-core kernel on its own copies and products
+ * is bounded (2 s of wall time).  Should one run out, that launch stops issuing work,
+ * waits (bounded) for what it already issued, frees its tensor memory, writes NaN
+ * for the affected outputs and raises the plan's error word.  The call itself is
+ * asynchronous and cannot see this; the word is reported as FST_ETIMEOUT by
+ * fst_sync(), by fst_project_host() of that call, or by the next fst_project /
+ * fst_apply_prolate / fst_project_noalloc / fst_coeffs call on the plan, which then
+ * enqueues nothing.  Reporting clears the word.
  * batch == 0 is a no-op returning FST_OK.
  */
 fst_status fst_project(fst_plan_t plan, const void *y, void *out, int64_t batch,
@@ -223,13 +229,24 @@ fst_status fst_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const
  * signature runs directly and allocates; the second records the whole batch in a
  * CUDA graph on a private stream; later calls replay it on `stream` (set
  * FST_GRAPHS=0 in the environment to always launch directly).  Calls with
- * different signatures keep up to four recorded batches.
+ * different signatures keep up to four recorded batches.  A recorded batch is
+ * dropped when one of its plans is destroyed, and recorded again when a plan's
+ * workspace has been reallocated since (a larger fst_project call on it).
  * Errors: FST_EINVAL (NULL pointers, count < 0), FST_ENOMEM, FST_ECUDA.
  */
 fst_status fst_project_ragged(const fst_plan_t *plans, const void *const *y, void *const *out,
                               int64_t count, int dtype, void *stream);
 
-/* fst_destroy -- frees the plan and its device memory.  NULL-safe. */
+/*
+ * fst_sync -- waits for `stream`, then reports the plan's device error word: FST_ETIMEOUT
+ * (and clears the word) when a bounded device wait of an earlier call on the plan gave
+ * up (its outputs are NaN; see fst_project), FST_OK otherwise.  Errors: FST_EINVAL
+ * (NULL plan), FST_ECUDA (the stream failed).
+ */
+fst_status fst_sync(fst_plan_t plan, void *stream);
+
+/* fst_destroy -- frees the plan and its device memory, and drops the recorded
+ * fst_project_ragged batches that use it (after their launches finish).  NULL-safe. */
 fst_status fst_destroy(fst_plan_t plan);
 
 /* fst_last_error -- message of the last failing call on this host thread ("" if none). */
@@ -252,23 +269,30 @@ fst_status fst_reduced_tridiagonal(int64_t N, double W, int parity, int64_t *n,
 
 /*
  * fst_project_noalloc -- fst_project that allocates nothing.  The paper has no
- * counterpart; this exists for callers that cannot call cudaMalloc or cudaFree
- * when they project (code recorded into a CUDA graph, or a process whose memory
- * manager owns all device memory after start-up).  fst_project allocates its
- * scratch on demand on the plan's first call; this variant instead uses one
- * fixed array of fst_noalloc_scratch_bytes() = 128 MiB compiled into the
- * library (every GPU that loads the library holds it until the process exits).
+ * counterpart; this exists for callers that cannot call cudaMalloc or cudaFree when
+ * they project (for example a process whose memory manager owns all device memory
+ * after start-up, or a service that must not stall on the allocator mid-request).
+ * fst_project allocates its scratch on demand on the plan's first call; this
+ * variant instead uses one fixed array of fst_noalloc_scratch_bytes() = 128 MiB
+ * compiled into the library (every GPU that loads the library holds it until the
+ * process exits).
  *   Arguments, layout and results: as fst_project (device pointers).  The plan
  *   itself must already exist (fst_plan allocates).
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   (cudaGetSymbolAddress) with that device current, and looks it up again when the
+ *   device's context has changed (after a device reset); make that first call before
  *   any stream capture.
  *   Sharing: all calls share the one array and it keeps the last call's contents.
  *   Calls whose work overlaps on the GPU (different streams, or several host
  *   threads) race on it: serialise them.  Nothing in it needs clearing.
  *   Errors: as fst_project; FST_EINVAL (message "signal too long for the fixed
- *   scratch buffer") when one launch group of the four-step path needs more
- *   than the array holds (FP32 N > 2^22, FP64 N > 2^21), or for an emulated plan.
+ *   scratch buffer") when the scratch of the four-step path does not fit in the
+ *   array: one launch group (one to eight pairs of M-point transforms, M the FFT
+ *   length) must fit, so FP32 N > 2^22 and FP64 N > 2^21 are always rejected;
+ *   beside it, the FP32 tensor-core correction keeps per-pair partial sums
+ *   of about 8 (tc_slices + 1) rpad bytes, so large batches are rejected too (N =
+ *   65536, r = 22: about 25 KB per pair, beyond roughly 10,000 real signals).  An
+ *   emulated plan is rejected with FST_EINVAL.
  */
 fst_status fst_project_noalloc(fst_plan_t plan, const void *y, void *out, int64_t batch,
                                int64_t ld, int dtype, void *stream);

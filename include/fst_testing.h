@@ -27,6 +27,17 @@ fst_status fst_emu_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, c
 /* 1 if the plan runs on the host emulator, 0 otherwise (including NULL). */
 int fst_plan_is_emulated(fst_plan_t plan);
 
+/*
+ * Test hook for the failure path of the bounded device waits (no GPU fault involved):
+ * the next `launches` launches of the tensor-core correction first wait on a barrier
+ * that nothing completes, give up after limit_s seconds (0 < limit_s <= 2) before
+ * issuing any copy or product, and take the kernel's normal give-up path (tensor
+ * memory freed, NaN partial sums, error word raised).  Calls made while a stall is
+ * pending launch directly (no CUDA graph is recorded or replayed).
+ * Errors: FST_EINVAL (launches < 0 or limit_s out of range).
+ */
+fst_status fst_test_tc_stall(int launches, double limit_s);
+
 #ifdef __cplusplus
 }
 #endif

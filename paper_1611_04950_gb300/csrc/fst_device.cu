@@ -8,11 +8,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "fst_internal.h"
+#include "../../include/fst_testing.h"
 #include "fst_fast.cuh"
 #define FST_TC_KERNELS
 #include "fst_tc.cuh"
@@ -376,6 +378,18 @@ static fst_status encode_2d(CUtensorMap *m, const void *base, uint64_t inner, ui
   return FST_OK;
 }
 
+// test hook (fst_test_tc_stall): the next g_tc_stall launches of the tcgen05 correction give
+// up after g_tc_stall_limit_ns on a wait that nothing completes
+static std::atomic<int> g_tc_stall{0};
+static unsigned long long g_tc_stall_limit_ns = 20000000ull;
+bool tc_stall_pending() { return g_tc_stall.load() > 0; }
+bool tc_stall_take() {
+  int v = g_tc_stall.load();
+  while (v > 0)
+    if (g_tc_stall.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 static inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
@@ -384,23 +398,34 @@ static inline int grid_for(int64_t n, int block) {
 struct DevRunner : Runner {
   cudaStream_t s = nullptr;     // caller's stream
   cudaStream_t cur = nullptr;   // stream the apply kernels go to (s, or a capture lane)
-  cudaStream_t cap[2] = {nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join = nullptr, ev_mid = nullptr;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};   // two lanes and the side lane
+  cudaEvent_t fork = nullptr, join = nullptr, ev_mid = nullptr, ev_side = nullptr, join_side = nullptr;
   bool capturing = false;
   long long launches_at_begin = 0;
   int sms = 1;
-  int *tc_err = nullptr;   // raised by k_corr_tc when one of its waits timed out
+  // raised by k_corr_tc when one of its waits timed out: a host-mapped word, so the host
+  // reads it without a copy (fst_sync, and the next call on the plan)
+  int *tc_err = nullptr;     // device address
+  int *tc_err_h = nullptr;   // host address
   bool device() const override { return true; }
   int sm_count() const override { return sms; }
   void set_stream(void *st) override { s = (cudaStream_t)st; cur = s; }
   void *stream() const override { return (void *)s; }
   ~DevRunner() override {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
       if (cap[i]) cudaStreamDestroy(cap[i]);
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (ev_mid) cudaEventDestroy(ev_mid);
-    if (tc_err) cudaFree(tc_err);
+    for (cudaEvent_t e : {fork, join, ev_mid, ev_side, join_side})
+      if (e) cudaEventDestroy(e);
+    if (tc_err_h) cudaFreeHost(tc_err_h);
+  }
+  fst_status device_status(bool sync) override {
+    if (sync) CU(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (tc_err_h && *(volatile int *)tc_err_h) {
+      *(volatile int *)tc_err_h = 0;
+      return fail(FST_ETIMEOUT, "a bounded wait of the tensor-core correction ran past its limit; the outputs "
+                                "of that call are NaN");
+    }
+    return FST_OK;
   }
 
   int lanes() const override { return capturing ? 2 : 1; }
@@ -415,6 +440,13 @@ struct DevRunner : Runner {
     cudaEventRecord(ev_mid, cap[1]);
     cudaStreamWaitEvent(cap[0], ev_mid, 0);
   }
+  void use_side() override { cur = capturing ? cap[2] : s; }
+  void side_done() override {
+    if (capturing) cudaEventRecord(ev_side, cap[2]);
+  }
+  void wait_side() override {
+    if (capturing) cudaStreamWaitEvent(cur, ev_side, 0);
+  }
   bool user_stream_capturing() override {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
@@ -425,14 +457,13 @@ struct DevRunner : Runner {
   }
   bool graph_begin() override {
     if (!cap[0]) {
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 3; ++i)
         if (cudaStreamCreateWithFlags(&cap[i], cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return false; }
-      if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ev_mid, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-      }
+      for (cudaEvent_t *e : {&fork, &join, &ev_mid, &ev_side, &join_side})
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          return false;
+        }
     }
     if (set_attrs() != FST_OK) return false;
     if (cudaStreamBeginCapture(cap[0], cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -441,6 +472,7 @@ struct DevRunner : Runner {
     }
     cudaEventRecord(fork, cap[0]);
     cudaStreamWaitEvent(cap[1], fork, 0);
+    cudaStreamWaitEvent(cap[2], fork, 0);
     capturing = true;
     cur = cap[0];
     launches_at_begin = g_launches;
@@ -450,6 +482,8 @@ struct DevRunner : Runner {
     *exec = nullptr;
     cudaEventRecord(join, cap[1]);
     cudaStreamWaitEvent(cap[0], join, 0);
+    cudaEventRecord(join_side, cap[2]);
+    cudaStreamWaitEvent(cap[0], join_side, 0);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap[0], &g);
     capturing = false;
@@ -597,9 +631,10 @@ struct DevRunner : Runner {
   fst_status tc_prep(const float *ST, int64_t N, int rpad, int r, int nB, int64_t Npad, float *STt) override {
     // plan time (never inside a stream capture): kernel attributes and the error word
     TRY(set_attrs());
-    if (!tc_err) {
-      CU(cudaMalloc((void **)&tc_err, sizeof(int)), "cudaMalloc");
-      CU(cudaMemset(tc_err, 0, sizeof(int)), "cudaMemset");
+    if (!tc_err_h) {
+      CU(cudaHostAlloc((void **)&tc_err_h, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+      *(volatile int *)tc_err_h = 0;
+      CU(cudaHostGetDevicePointer((void **)&tc_err, tc_err_h, 0), "cudaHostGetDevicePointer");
     }
     k_tc_prep<<<grid_for((int64_t)nB * Npad, 256), 256, 0, s>>>(ST, N, rpad, r, nB, Npad, STt);
     LAUNCHED("k_tc_prep");
@@ -629,6 +664,12 @@ struct DevRunner : Runner {
     t.nitems = (int)(t.nks * rb);
     t.part = a.part;
     t.err = tc_err;
+    t.timeout_ns = TC_TIMEOUT_NS;
+    t.stall = 0;
+    if (tc_stall_take()) {
+      t.stall = 1;
+      t.timeout_ns = g_tc_stall_limit_ns;
+    }
     // persistent: one CTA per SM walks the items
     dim3 grid((unsigned)std::min<int64_t>(t.nitems, sms));
     const size_t smem = (size_t)tc_smem_bytes(t.nB);
@@ -846,13 +887,12 @@ using namespace fst;
 extern "C" long long fst_launch_count(void) { return g_launches; }
 
 // ---------------------------------------------------------------------------
-// fst_project_noalloc: fst_project for callers that cannot allocate device
-// memory at call time (for example code running inside a CUDA-graph capture or
-// under an allocator that forbids cudaMalloc/cudaFree after start-up).  The
-// four-step path's scratch (intermediate spectra, per-tile partial sums and the
-// correction coefficients) lives in one fixed file-scope device array instead of
-// the plan's on-demand workspace.  Every device that loads this library holds the
-// array until the process exits.
+// fst_project_noalloc: fst_project for callers that cannot allocate device memory
+// when they project (for example a process whose memory manager owns all device
+// memory after start-up).  The four-step path's scratch (intermediate spectra,
+// per-tile partial sums and the correction coefficients) lives in one fixed
+// file-scope device array instead of the plan's on-demand workspace.  Every device
+// that loads this library holds the array until the process exits.
 // ---------------------------------------------------------------------------
 #define FST_NOALLOC_SCRATCH_BYTES (128ull << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FST_NOALLOC_SCRATCH_BYTES];
@@ -861,6 +901,26 @@ namespace {
 constexpr int kMaxDevices = 128;
 std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};   // context the address was looked up in
+// the calling thread's current context (the primary context of the current device,
+// re-created after a device reset)
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext *);
+  static Fn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (Fn)p;
+    else
+      cudaGetLastError();
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 }  // namespace
 
 extern "C" fst_status fst_project_noalloc(fst_plan_t p, const void *y, void *out, int64_t batch, int64_t ld,
@@ -872,13 +932,16 @@ extern "C" fst_status fst_project_noalloc(fst_plan_t p, const void *y, void *out
   if (dev < 0 || dev >= kMaxDevices) return fail(FST_EUNSUPPORTED, "device ordinal out of range");
   void *scratch = nullptr;
   {
-    // one-time set-up per device (with that device current): the host-side name of
-    // the array is only a stand-in, its device address comes from the runtime
+    // set-up per device and context (with that device current): the host-side name of
+    // the array is only a stand-in, its device address comes from the runtime; a new
+    // context (after a device reset) gets the array at a new address
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
       void *a = nullptr;
       CU(cudaGetSymbolAddress(&a, g_noalloc_scratch), "cudaGetSymbolAddress");
       g_scratch_addr[dev] = a;
+      g_scratch_ctx[dev] = current_context();   // the runtime has made its context current
     }
     scratch = g_scratch_addr[dev];
   }
@@ -1005,7 +1068,7 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
   }
   CU(cudaStreamSynchronize(hp.cout), "sync");
   CU(cudaStreamSynchronize(sc), "sync");
-  return FST_OK;
+  return p->R->device_status(false);
 }
 
 // ---------------------------------------------------------------------------
@@ -1016,14 +1079,27 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
 namespace {
 struct RaggedCtx {
   std::vector<const void *> sig;
-  std::vector<void *> bufs;
-  fst::Runner *R = nullptr;   // runner that owns bufs
+  std::vector<fst_plan_t> plans;   // the batch's plans, in call order
+  std::vector<uint64_t> gens;      // their workspace generations when the graph was recorded
+  std::vector<void *> bufs;        // descriptor arrays (cudaMalloc), owned by the context
   cudaGraphExec_t exec = nullptr;
   long long nodes = 0;
   int seen = 0;
 };
-std::mutex g_ragged_mu;
+std::recursive_mutex g_ragged_mu;
 std::vector<RaggedCtx *> g_ragged;
+// frees a context after every launch that may still use it has finished
+void free_ctx(RaggedCtx *c) {
+  cudaDeviceSynchronize();
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  for (void *b : c->bufs) cudaFree(b);
+  delete c;
+}
+bool ctx_current(const RaggedCtx *c) {
+  for (size_t i = 0; i < c->plans.size(); ++i)
+    if (c->plans[i]->ws_gen != c->gens[i]) return false;
+  return true;
+}
 cudaStream_t g_ragged_cap = nullptr;
 bool ragged_graphs_enabled() {
   const char *s = getenv("FST_GRAPHS");
@@ -1043,7 +1119,7 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
     for (void *b : bufs) plans[0]->R->release(b);
     return st;
   }
-  std::lock_guard<std::mutex> lk(g_ragged_mu);
+  std::lock_guard<std::recursive_mutex> lk(g_ragged_mu);
   std::vector<const void *> sig;
   sig.reserve(3 * count + 1);
   sig.push_back((const void *)(intptr_t)dtype);
@@ -1062,6 +1138,13 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
     cs = cudaStreamCaptureStatusActive;
   }
   const bool graphs = ragged_graphs_enabled() && !profiling_enabled() && cs == cudaStreamCaptureStatusNone;
+  if (ctx && ctx->exec && !ctx_current(ctx)) {
+    // a plan's workspace moved since the recording: run directly, record again next time
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(ctx->exec);
+    ctx->exec = nullptr;
+    ctx->seen = 0;
+  }
   if (ctx && ctx->exec && graphs) {
     CU(cudaGraphLaunch(ctx->exec, us), "cudaGraphLaunch");
     g_launches += ctx->nodes;
@@ -1069,16 +1152,12 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
   }
   if (!ctx) {
     if (g_ragged.size() >= 4) {
-      RaggedCtx *old = g_ragged.front();
-      cudaStreamSynchronize(us);
-      if (old->exec) cudaGraphExecDestroy(old->exec);
-      for (void *b : old->bufs) old->R->release(b);
-      delete old;
+      free_ctx(g_ragged.front());
       g_ragged.erase(g_ragged.begin());
     }
     ctx = new RaggedCtx();
     ctx->sig = sig;
-    ctx->R = plans[0]->R;
+    ctx->plans.assign(plans, plans + count);
     g_ragged.push_back(ctx);
   }
   for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream(stream);
@@ -1105,7 +1184,33 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
   e = cudaGraphInstantiate(&ctx->exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  ctx->gens.resize(count);
+  for (int64_t i = 0; i < count; ++i) ctx->gens[i] = plans[i]->ws_gen;
   CU(cudaGraphLaunch(ctx->exec, us), "cudaGraphLaunch");
   g_launches += ctx->nodes;
+  return FST_OK;
+}
+
+namespace fst {
+// A plan about to be destroyed: every recorded ragged batch that uses it points at its
+// device data and is dropped (after its launches finish), with its descriptor arrays.
+void forget_ragged(fst_plan_t p) {
+  std::lock_guard<std::recursive_mutex> lk(g_ragged_mu);
+  for (size_t i = 0; i < g_ragged.size();) {
+    RaggedCtx *c = g_ragged[i];
+    if (std::find(c->plans.begin(), c->plans.end(), p) != c->plans.end()) {
+      free_ctx(c);
+      g_ragged.erase(g_ragged.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+}  // namespace fst
+
+extern "C" fst_status fst_test_tc_stall(int launches, double limit_s) {
+  if (launches < 0 || !(limit_s > 0.0) || limit_s > 2.0) return fail(FST_EINVAL, "bad stall request");
+  fst::g_tc_stall_limit_ns = (unsigned long long)(limit_s * 1e9);
+  fst::g_tc_stall.store(launches);
   return FST_OK;
 }

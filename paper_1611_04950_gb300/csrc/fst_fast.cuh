@@ -89,13 +89,63 @@ template <bool INV> struct RegDft<32, INV> {
   }
 };
 
-// P-point DFT of column n2 (v), times W_M^{n2 k1}, stored to inter[row0 + k1 Q + n2].
+// exp(-+2 pi i n / P) for P in {8, 16, 32}, n < P (compile-time n: folds to constants)
+template <int P, bool INV> __device__ __forceinline__ float2 wP(int n) {
+  constexpr double C[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                           0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                           0.19509032201612826785, 0.0};   // cos(2 pi k / 32), k = 0..8
+  const int k = n * (32 / P), q = k >> 3, r = k & 7;
+  const double c = C[r], sn = C[8 - r];                    // cos, sin of 2 pi r / 32
+  double re, im;                                           // cos, sin of 2 pi k / 32
+  if (q == 0) { re = c; im = sn; } else if (q == 1) { re = -sn; im = c; }
+  else if (q == 2) { re = -c; im = -sn; } else { re = sn; im = -c; }
+  return make_float2((float)re, INV ? (float)im : (float)-im);
+}
+
+// Forward P-point DFT of a column whose rows n >= P/2 are zero (M >= 2N): with e = x and
+// o[n] = x[n] W_P^n (n < P/2), X[2m] = DFT_{P/2}(e)[m] and X[2m+1] = DFT_{P/2}(o)[m].
+// In: v[0 .. P/2); out: v[0 .. P) in natural order.
+template <int P> __device__ __forceinline__ void dft_half_in(float2 *v) {
+  constexpr int H = P / 2;
+  // o in the upper half (its rows are zero on input), e in place
+#pragma unroll
+  for (int n = 0; n < H; ++n) v[H + n] = (n == 0) ? v[0] : cmul(v[n], wP<P, false>(n));
+  Dft<float, H, false>::run(v);
+  Dft<float, H, false>::run(v + H);
+  float2 t[P];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    t[2 * m] = v[m];
+    t[2 * m + 1] = v[H + m];
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) v[k] = t[k];
+}
+
+// The first P/2 outputs of the inverse P-point DFT of v (natural order in), into out:
+// X[n] = IDFT_{P/2}(even rows)[n] + W_P^{-n} IDFT_{P/2}(odd rows)[n], n < P/2.
+template <int P> __device__ __forceinline__ void idft_half_out(const float2 *v, float2 *out) {
+  constexpr int H = P / 2;
+  float2 e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    e[k] = v[2 * k];
+    o[k] = v[2 * k + 1];
+  }
+  Dft<float, H, true>::run(e);
+  Dft<float, H, true>::run(o);
+#pragma unroll
+  for (int n = 0; n < H; ++n) out[n] = cadd(e[n], (n == 0) ? o[0] : cmul(o[n], wP<P, true>(n)));
+}
+
+// P-point DFT of column n2 (v; rows n1 >= P/2 zero), times W_M^{n2 k1}, stored to
+// inter[row0 + k1 Q + n2].
 // k1 = 8h + b, W^{k1} = W^{8h} W^b: table lookups for W, W^8, W^16, small powers by at most
 // two products, applied and stored right away.
 template <int P>
 __device__ __forceinline__ void fastA_finish(const ConvArgs<float> &a, float2 *v, int64_t row0, int64_t n2) {
   const int Q = 1 << a.log2Q;
-  RegDft<P, false>::run(v);
+  dft_half_in<P>(v);
   float2 *dst = a.inter + row0 + n2;
   const float2 w1 = a.tw.root<false>((uint64_t)n2, a.log2M);
   const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
@@ -471,19 +521,19 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
   }
 
   if (!live) return;
-  float2 v[P];
+  float2 o[P / 2];   // inverse DFT outputs n1 < P/2 (M >= 2N: no output in the other rows)
   {
     const float2 *src = a.inter + ((g0 + g) * P) * (int64_t)Q + n2;
+    float2 v[P];
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) v[k1] = src[(int64_t)k1 * Q];
-    RegDft<P, true>::run(v);
+    idft_half_out<P>(v, o);
   }
-  float *outp = a.out;
 #pragma unroll
   for (int n1 = 0; n1 < P / 2; ++n1) {
     const int64_t n = (int64_t)n1 * Q + n2;
     if (n1 < a.Pnz && n < a.N) {
-      float2 val = v[n1];
+      float2 val = o[n1];
       if (corr) {
         val.x += zt[n1 * 32 + c][2 * g];
         val.y += zt[n1 * 32 + c][2 * g + 1];
@@ -491,7 +541,6 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastC(const FastArgs f) {
       store_pair(a, g0 + g, n, val);
     }
   }
-  (void)outp;
 }
 
 }  // namespace fst

@@ -129,10 +129,18 @@ static bool tc_disabled() {
   return s && s[0] == '0';
 }
 
+// FST_PLAIN=1: the plain FP32 form the batched path is compared with -- generic four-step
+// kernels with the rank-r correction on CUDA cores inside the column passes, launched
+// directly (no CUDA graph, no tensor cores); read at every call
+static bool plain_mode() {
+  const char *s = getenv("FST_PLAIN");
+  return s && s[0] == '1';
+}
+
 // the tcgen05 correction applies: FP32 device plan with K-major S_T^T tiles and signal rows
 // a TMA tensor map can address (16-byte aligned base and row stride)
 static bool tc_usable(const ConvArgs<float> &a) {
-  if (!a.STt || tc_disabled()) return false;
+  if (!a.STt || tc_disabled() || plain_mode()) return false;
   const int64_t row_bytes = a.ld * (a.cplx ? 8 : 4);
   return ((uintptr_t)a.y % 16) == 0 && row_bytes % 16 == 0 && a.N < (1LL << 30) && a.batch < (1LL << 31);
 }
@@ -178,11 +186,14 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     sc.npairs = npairs;
     sc.part = (float *)w;
     sc.acoef = (float *)(w + (size_t)npairs * nK * 2 * a.rpad * sizeof(float));
+    // on the side lane: only the passes that write the output (pass C, or the last
+    // S_T a pass) wait for the coefficients, so the correction overlaps the first passes
+    R->use_side();
     TRY(corr_coefficients(R, sc, (const float *)a.D));
+    R->side_done();
     a.mode = L.fast ? MODE_ZONLY : MODE_CONV;
-    // every launch group, on either lane, runs after the coefficients
-    R->lanes_after_first();
   }
+  bool waited[2] = {false, false};
   int64_t group = 0;
   for (int64_t p0 = 0; p0 < npairs; p0 += L.chunk, ++group) {
     const int lane = (int)(group % lanes);
@@ -203,6 +214,10 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
       TRY(R->passA(a, L));
       if (a.mode == MODE_FULL && a.r > 0 && !(L.fused_reduce && R->device())) TRY(R->reduce(a, L));
       TRY(R->passB(a, L));
+      if (split && L.fast && !waited[lane]) {
+        R->wait_side();
+        waited[lane] = true;
+      }
       if (a.mode != MODE_FORWARD) TRY(R->passC(a, L));
     }
   }
@@ -210,6 +225,7 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
   if (split && !L.fast) {
     // out += S_T a over the whole batch once both lanes have written B y
     R->lanes_join_first();
+    R->wait_side();
     // CUDA-core pass when the batch has enough signal rows to share each staged S_T block
     // (measured: faster from 64 rows up, slower for 16)
     const int64_t zrows = sc.cplx ? 2 * sc.batch : sc.batch;
@@ -231,9 +247,10 @@ static bool graphs_enabled() {
 
 static fst_status ensure_ws(fst_plan_t p, size_t bytes) {
   if (bytes <= p->ws_bytes) return FST_OK;
-  // the cached graphs point at the old workspace
+  // the cached graphs point at the old workspace (recorded ragged batches check ws_gen)
   for (auto &e : p->graphs) p->R->graph_destroy(e.exec);
   p->graphs.clear();
+  ++p->ws_gen;
   if (p->ws) p->R->release(p->ws);
   p->ws = nullptr;
   p->ws_bytes = 0;
@@ -277,8 +294,15 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
     Layout L1 = L0;
     if (!L1.small) L1.chunk = std::min<int64_t>(L0.chunk, (npairs + L0.G - 1) / L0.G * L0.G);
     const Layout &Lc = L1;
+    if (plain_mode() && !dbl && R->device() && !L0.small) {
+      Layout Lp = make_layout(p->N, p->log2M, false, (int)p->rpad, false);
+      Lp.chunk = std::min<int64_t>(Lp.chunk, (npairs + Lp.G - 1) / Lp.G * Lp.G);
+      TRY(ensure_ws(p, ws_need(Lp, false, (int)p->rpad, false)));
+      return run_conv<T>(R, Lp, a, npairs, p->ws);
+    }
     const size_t slot = ws_need(Lc, dbl, (int)p->rpad, false);
-    const bool graphs = R->device() && graphs_enabled() && !profiling_enabled() && !R->user_stream_capturing();
+    const bool graphs = R->device() && graphs_enabled() && !profiling_enabled() && !tc_stall_pending() &&
+                        !R->user_stream_capturing();
     if (!graphs) {
       TRY(ensure_ws(p, slot + extra));
       return run_conv<T>(R, Lc, a, npairs, p->ws);
@@ -333,6 +357,7 @@ fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, i
   if (!y || !out) return fail(FST_EINVAL, "NULL signal pointer");
   if (ld == 0) ld = p->N;
   if (ld < p->N) return fail(FST_EINVAL, "ld < N");
+  TRY(p->R->device_status(false));
   switch (dtype) {
     case FST_F32:
       return apply_t<float>(p, (const float *)y, (float *)out, batch, ld, false, full, p->spec32, p->ST32, p->D32,
@@ -788,6 +813,7 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
 
 void destroy_plan(fst_plan_t p) {
   if (!p) return;
+  forget_ragged(p);
   if (p->R) free_coef(p);
   Runner *R = p->R;
   if (R) {
@@ -871,6 +897,12 @@ fst_status fst_apply_prolate(fst_plan_t p, const void *y, void *out, int64_t bat
 fst_status fst_destroy(fst_plan_t p) {
   destroy_plan(p);
   return FST_OK;
+}
+
+fst_status fst_sync(fst_plan_t p, void *stream) {
+  if (!p) return fail(FST_EINVAL, "plan is NULL");
+  p->R->set_stream(stream);
+  return p->R->device_status(true);
 }
 
 fst_status fst_reduced_tridiagonal(int64_t N, double W, int parity, int64_t *n, double *d, double *e) {
@@ -1300,6 +1332,7 @@ static fst_status run_coeffs(fst_plan_t p, const void *y, void *out, int64_t bat
   if (ld < p->N) return fail(FST_EINVAL, "ld < N");
   if (p->op != FST_OP_PROJECT) return fail(FST_EINVAL, "coefficients need a projection plan");
   if ((p->N & (p->N - 1)) != 0) return fail(FST_EUNSUPPORTED, "coefficients need N a power of two");
+  TRY(p->R->device_status(false));
   switch (dtype) {
     case FST_F32: return coeffs_t<float>(p, (const float *)y, (float2 *)out, batch, ld, false);
     case FST_C64: return coeffs_t<float>(p, (const float *)y, (float2 *)out, batch, ld, true);

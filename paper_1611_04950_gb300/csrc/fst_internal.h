@@ -39,6 +39,12 @@ struct Runner {
   virtual void lanes_after_first() {}
   // order lane 0 after everything lane 1 has issued so far
   virtual void lanes_join_first() {}
+  // side lane (capture only): the separate correction runs there, beside the first passes
+  // of the launch groups; side_done() marks its end and wait_side() orders the current lane
+  // after that mark.  Without a capture all of it is one stream (no-ops).
+  virtual void use_side() {}
+  virtual void side_done() {}
+  virtual void wait_side() {}
   virtual fst_status alloc(void **p, size_t bytes) = 0;
   virtual void release(void *p) = 0;
   virtual fst_status h2d(void *dst, const void *src, size_t bytes) = 0;
@@ -46,6 +52,9 @@ struct Runner {
   virtual fst_status d2d(void *dst, const void *src, size_t bytes) = 0;
   virtual fst_status zero(void *p, size_t bytes) = 0;
   virtual fst_status sync() = 0;
+  // FST_ETIMEOUT (and clears it) when a bounded device wait of an earlier launch gave up;
+  // with `sync`, first waits for the runner's stream
+  virtual fst_status device_status(bool sync) { return sync ? this->sync() : FST_OK; }
 
   virtual fst_status small(const ConvArgs<float> &a, const Layout &L) = 0;
   virtual fst_status small(const ConvArgs<double> &a, const Layout &L) = 0;
@@ -161,6 +170,7 @@ struct fst_plan_s {
   double2 *tw64h = nullptr, *tw64l = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  uint64_t ws_gen = 0;   // bumped whenever ws is reallocated (recorded graphs point into it)
   std::vector<int64_t> idx;
   std::vector<double> lam, D;
   std::vector<double> lam_window;
@@ -194,6 +204,11 @@ bool profiling_enabled();   // per-launch event timing is on (fst_profile_enable
 // to desc_bufs (the caller owns them); buffers already in desc_bufs are reused
 fst_status run_ragged(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count, int dtype,
                       std::vector<void *> &desc_bufs);
+// drop every recorded ragged batch that uses plan p (before p or its workspace is freed)
+void forget_ragged(fst_plan_t p);
+// a test-requested stall of the tcgen05 correction is pending / consume one
+bool tc_stall_pending();
+bool tc_stall_take();
 fst_status build_plans_many(Runner *(*mk)(), void *stream, int64_t count, const int64_t *N, const double *W,
                             const int64_t *K, const double *eps, fst_plan_t *out);
 }  // namespace fst

@@ -55,7 +55,9 @@ struct TcArgs {
   int nks;         // interleaved slices
   int nitems;      // nks x row blocks
   float *part;     // [pair][nks][2][rpad]
-  int *err;        // set to 1 when a wait timed out
+  int *err;        // set to 1 when a wait timed out (host-mapped word, read by the host)
+  unsigned long long timeout_ns;   // limit of every mbarrier wait (TC_TIMEOUT_NS)
+  int stall;       // test hook: the producer first waits on a barrier nothing completes
 };
 
 // raw ring stage (shared memory): y tile + S tile; operand stage: S hi + S lo in shared
@@ -130,14 +132,15 @@ __device__ __forceinline__ bool tc_mbar_try(uint32_t bar, uint32_t parity) {
 }
 // Wait for the phase of `bar` with the given parity.  Returns false when the CTA gave up:
 // either the shared abort flag is up (honoured only if `honour_abort`) or this wait ran
-// past the time limit, which raises the flag.
-__device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, bool honour_abort) {
+// past `limit_ns` of wall time, which raises the flag.
+__device__ __noinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, bool honour_abort,
+                                     unsigned long long limit_ns) {
   if (tc_mbar_try(bar, parity)) return true;
   const uint64_t t0 = tc_gtimer();
   for (;;) {
     if (tc_mbar_try(bar, parity)) return true;
     if (honour_abort && *abort_flag) return false;
-    if (tc_gtimer() - t0 > TC_TIMEOUT_NS) {
+    if (tc_gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t bars = opb + RB * SO;
   const uint32_t fullA = bars, freeA = bars + 64, fullB = bars + 128, emptyB = bars + 160;
   const uint32_t afull0 = bars + 192, aempty0 = bars + 208, done = bars + 224;
+  const uint32_t stall = bars + 240;   // test hook only: never completed
   uint8_t *gbars = gbase + (bars - base);
   uint32_t *tslot = (uint32_t *)(gbars + 232);
   volatile int *abort_flag = (volatile int *)(gbars + 236);
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_mbar_init(aempty0 + 8 * c, TC_WORKERS);
     }
     tc_mbar_init(done, 1);
+    tc_mbar_init(stall, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -284,11 +289,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int i = 0, issued = 0;
       bool go = true;
+      // test hook: give up before the first copy, on a wait that nothing can complete
+      if (t.stall) go = tc_wait(stall, 0u, abort_flag, true, t.timeout_ns);
       for (int it = blockIdx.x; it < t.nitems && go; it += gridDim.x) {
         const TcItem x = tc_item(t, it);
         for (int tt = 0; tt < x.ntile; ++tt, ++i) {
           const int a = i % RA;
-          if (i >= RA && !tc_wait(freeA + 8 * a, (uint32_t)((i / RA) - 1) & 1u, abort_flag, true)) {
+          if (i >= RA && !tc_wait(freeA + 8 * a, (uint32_t)((i / RA) - 1) & 1u, abort_flag, true, t.timeout_ns)) {
             go = false;
             break;
           }
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // the copies issued last must land before the CTA may exit
       for (int j = max(0, issued - RA); j < issued; ++j)
-        tc_wait(fullA + 8 * (j % RA), (uint32_t)(j / RA) & 1u, abort_flag, false);
+        tc_wait(fullA + 8 * (j % RA), (uint32_t)(j / RA) & 1u, abort_flag, false, t.timeout_ns);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -323,11 +330,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int tt = 0; tt < x.ntile; ++tt, ++i) {
           const int b = i % RB, c = g & 1;
           const bool first = (tt % TC_GROUP) == 0;
-          if (first && g >= 2 && !tc_wait(aempty0 + 8 * c, (uint32_t)((g / 2) - 1) & 1u, abort_flag, true)) {
+          if (first && g >= 2 && !tc_wait(aempty0 + 8 * c, (uint32_t)((g / 2) - 1) & 1u, abort_flag, true, t.timeout_ns)) {
             go = false;
             break;
           }
-          if (!tc_wait(fullB + 8 * b, (uint32_t)(i / RB) & 1u, abort_flag, true)) {
+          if (!tc_wait(fullB + 8 * b, (uint32_t)(i / RB) & 1u, abort_flag, true, t.timeout_ns)) {
             go = false;
             break;
           }
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // add finished group g (of item it; the item's last group if `last`) into the sums
     auto drain = [&](int g, int it, bool last) {
       const int c = g & 1;
-      if (ok) ok = tc_wait(afull0 + 8 * c, (uint32_t)(g / 2) & 1u, abort_flag, true);
+      if (ok) ok = tc_wait(afull0 + 8 * c, (uint32_t)(g / 2) & 1u, abort_flag, true, t.timeout_ns);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
         tc_fence_after();
@@ -432,8 +439,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const TcItem x = tc_item(t, it);
       for (int tt = 0; tt < x.ntile; ++tt, ++i) {
         const int a = i % RA, b = i % RB;
-        if (ok) ok = tc_wait(fullA + 8 * a, (uint32_t)(i / RA) & 1u, abort_flag, true);
-        if (ok && i >= RB) ok = tc_wait(emptyB + 8 * b, (uint32_t)((i / RB) - 1) & 1u, abort_flag, true);
+        if (ok) ok = tc_wait(fullA + 8 * a, (uint32_t)(i / RA) & 1u, abort_flag, true, t.timeout_ns);
+        if (ok && i >= RB) ok = tc_wait(emptyB + 8 * b, (uint32_t)((i / RB) - 1) & 1u, abort_flag, true, t.timeout_ns);
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
           tc_fence_after();
@@ -503,7 +510,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (g >= 1) drain(g - 1, prev_it, prev_last);
     // every product must retire before the TMEM is released
-    tc_wait(done, 0u, abort_flag, false);
+    tc_wait(done, 0u, abort_flag, false, t.timeout_ns);
   }
   tc_fence_before();
   __syncthreads();
@@ -511,7 +518,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
-  if (threadIdx.x == 0 && *abort_flag) atomicExch(t.err, 1);
+  if (threadIdx.x == 0 && *abort_flag) {
+    *(volatile int *)t.err = 1;
+    __threadfence_system();
+  }
 }
 
 // S_T^T in FP32, K-major: STt[j][n] (zero for j >= r, n >= N)

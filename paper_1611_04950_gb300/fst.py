@@ -34,7 +34,8 @@ EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_
             "fst_reduced_tridiagonal", "fst_emu_plan_op", "fst_plan_is_emulated",
             "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
             "fst_project_noalloc", "fst_noalloc_scratch_bytes", "fst_coeffs", "fst_coeffs_info",
-            "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged", "fst_expand"]
+            "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged", "fst_expand",
+            "fst_sync", "fst_test_tc_stall"]
 
 
 class FSTError(RuntimeError):
@@ -57,6 +58,8 @@ def _load():
         "fst_project_host": ([P, vp, vp, i64, I, vp], I),
         "fst_apply_prolate": ([P, vp, vp, i64, i64, I, vp], I),
         "fst_destroy": ([P], I),
+        "fst_sync": ([P, vp], I),
+        "fst_test_tc_stall": ([I, d], I),
         "fst_last_error": ([], C.c_char_p),
         "fst_version": ([], C.c_char_p),
         "fst_reduced_tridiagonal": ([i64, d, I, C.POINTER(i64), C.POINTER(d), C.POINTER(d)], I),
@@ -252,6 +255,18 @@ class PlanSet:
 
 def fst_destroy(h: int):
     _check(_lib.fst_destroy(C.c_void_p(h)))
+
+
+def fst_sync(h: int, stream: int = 0):
+    """Waits for `stream`; raises FSTError(FST_ETIMEOUT) if a bounded device wait of an
+    earlier call on the plan gave up."""
+    _check(_lib.fst_sync(C.c_void_p(h), C.c_void_p(stream)))
+
+
+def fst_test_tc_stall(launches: int, limit_s: float = 0.02):
+    """Test hook: the next `launches` tensor-core correction launches give up on a wait that
+    nothing completes, after limit_s seconds, before issuing any work."""
+    _check(_lib.fst_test_tc_stall(launches, limit_s))
 
 
 def fst_launch_count() -> int:

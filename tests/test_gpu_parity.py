@@ -95,20 +95,28 @@ def test_c65k_small_batch():
     assert np.all(rel_err(out, ref, y) <= wl.eps + 1e-5)
 
 
-def test_c65k_full_batch_sampled():
-    # the benchmark's launch configuration: 1024 signals in one call, samples checked
-    dev = _cuda()
+def _fast_rows(o, y, chunk=128):
+    """Oracle fast projection of the rows of y (FP64), in chunks of rows."""
+    out = np.empty(y.shape, dtype=np.complex128 if np.iscomplexobj(y) else np.float64)
+    for i in range(0, y.shape[0], chunk):
+        out[i:i + chunk] = O.fast_project(o, y[i:i + chunk].T).T
+    return out
+
+
+def test_c65k_full_batch_every_row():
+    # the benchmark's launch configuration: 1024 signals in one call (every tcgen05 row block,
+    # launch group and column tile), every row against the FP64 oracle
+    _cuda()
     wl = workloads.c65k(batch=1024, device="cuda")
     p = F.Plan(wl.N, wl.W, eps=wl.eps)
     out = p.project(wl.y)
     torch.cuda.synchronize()
+    F.fst_sync(p.h, 0)
     o = oplan(wl.N, wl.W, p.K, wl.eps)
-    idx = [0, 1, 511, 512, 513, 1023]
-    y = wl.y[idx].double().cpu().numpy()
-    fast = O.fast_project(o, y.T).T
-    e = rel_err(out[idx].cpu().numpy(), fast, y)
-    assert np.all(e < 1e-5), e
-    assert torch.isfinite(out).all()
+    y = wl.y.double().cpu().numpy()
+    e = rel_err(out.cpu().numpy(), _fast_rows(o, y), y)
+    assert e.shape == (1024,)
+    assert np.all(e < 1e-5), (np.argmax(e), e.max())
 
 
 # ---------------------------------------------------------------- edge cases ------------
@@ -186,6 +194,27 @@ def test_other_operators(op, alpha, mul):
     assert np.max(np.abs(out - O.fast_apply(o, y.numpy().T).T)) < 1e-10
     exact = O.exact_operator_dense(N, W, p.K, op, alpha)
     assert np.all(rel_err(out, (exact @ y.numpy().T).T, y.numpy()) <= mul * eps + 1e-10)
+
+
+@pytest.mark.parametrize("op,alpha", [("pinv", 0.0), ("tikhonov", 1e-3)])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_other_operators_four_step(op, alpha, cplx):
+    # N = 65536: the four-step kernels with the pseudoinverse D (1/lambda - lambda on l < K) and
+    # with the Tikhonov scaling of the Toeplitz part (beta = 1/(1 + alpha) = 0.999, visible far
+    # above the tolerance), against the FP64 oracle
+    dev = _cuda()
+    N, W, eps = 65536, 1 / 8, 1e-5
+    p = F.Plan(N, W, eps=eps, op=op, alpha=alpha)
+    o = oplan(N, W, p.K, eps, op, alpha)
+    assert p.r == o.r
+    y = workloads.gaussian(6, N, seed=31, complex_=cplx)
+    ref = O.fast_apply(o, y.numpy().T).T
+    out = p.project(y.to(torch.complex64 if cplx else torch.float32).to(dev)).cpu().numpy()
+    assert np.all(rel_err(out, ref, y.numpy()) < 1e-5 * max(1.0, np.abs(o.D).max()))
+    if op == "tikhonov":
+        # without the 1/(1 + alpha) scaling the result would be off by ~alpha ||B y||
+        plain = O.fast_apply(oplan(N, W, p.K, eps), y.numpy().T).T
+        assert np.all(rel_err(out, plain, y.numpy()) > 1e-4)
 
 
 def test_degenerate_K_and_batch_zero():
@@ -316,7 +345,7 @@ def test_coeffs_complex_input():
 
 # ---------------------------------------------------------------- full-size workloads, sampled
 
-def test_c1m_complex_full_batch_sampled():
+def test_c1m_complex_full_batch_every_row():
     # N = 2^20, W = 0.05, eps = 1e-6, 64 complex64 signals (half band-limited), one call
     _cuda()
     wl = workloads.c1m(batch=64, device="cuda")
@@ -325,34 +354,51 @@ def test_c1m_complex_full_batch_sampled():
     torch.cuda.synchronize()
     o = oplan(wl.N, wl.W, p.K, wl.eps)
     assert p.r == o.r
-    idx = [0, 63]
-    y = wl.y[idx].to(torch.complex128).cpu().numpy()
-    fast = O.fast_project(o, y.T).T
-    e = rel_err(out[idx].cpu().numpy(), fast, y)
-    assert np.all(e < 1e-5), e
+    y = wl.y.to(torch.complex128).cpu().numpy()
+    e = rel_err(out.cpu().numpy(), _fast_rows(o, y, chunk=8), y)
+    assert e.shape == (64,)
+    assert np.all(e < 1e-5), (np.argmax(e), e.max())
 
 
-def test_c4m_full_batch_sampled_projection_and_coeffs():
-    # N = 2^22, W = 1/4, eps = 1e-8, 16 real FP32 signals: projection and coefficient vector
-    from oracle import thm1 as T
-    _cuda()
+@functools.lru_cache(maxsize=None)
+def _c4m():
     wl = workloads.c4m(batch=16, device="cuda")
     p = F.Plan(wl.N, wl.W, eps=wl.eps)
+    return wl, p
+
+
+def test_c4m_full_batch_projection_every_row_and_coeffs():
+    # N = 2^22, W = 1/4, eps = 1e-8, 16 real FP32 signals: every projected row, and the
+    # coefficient vector of four rows (both halves of the workload)
+    from oracle import thm1 as T
+    _cuda()
+    wl, p = _c4m()
     out = p.project(wl.y)
     coef = p.coeffs(wl.y)
     torch.cuda.synchronize()
     o = oplan(wl.N, wl.W, p.K, wl.eps)
     assert p.r == o.r
-    idx = [0, 15]
-    y = wl.y[idx].double().cpu().numpy()
-    fast = O.fast_project(o, y.T).T
-    e = rel_err(out[idx].cpu().numpy(), fast, y)
-    assert np.all(e < 1e-5), e
+    y = wl.y.double().cpu().numpy()
+    e = rel_err(out.cpu().numpy(), _fast_rows(o, y, chunk=4), y)
+    assert e.shape == (16,)
+    assert np.all(e < 1e-5), (np.argmax(e), e.max())
+    idx = [0, 7, 8, 15]
     t = T.thm1(wl.N, wl.W, wl.eps)
-    ref = T.coeffs(t, o, y.T).T
+    ref = T.coeffs(t, o, y[idx].T).T
     c = coef[idx].cpu().numpy()
     assert c.shape == ref.shape
-    assert np.all(np.abs(c - ref) <= 1e-5 * np.linalg.norm(y, axis=1)[:, None])
+    assert np.all(np.abs(c - ref) <= 1e-5 * np.linalg.norm(y[idx], axis=1)[:, None])
+
+
+def test_c4m_repeatable_bit_for_bit():
+    # the large tight-tolerance workload: projection and coefficient vector, run twice
+    _cuda()
+    wl, p = _c4m()
+    a, ca = p.project(wl.y), p.coeffs(wl.y)
+    b, cb = p.project(wl.y), p.coeffs(wl.y)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.equal(ca, cb)
 
 
 # ---------------------------------------------------------------- ragged batches

@@ -1,8 +1,9 @@
 """fst_project_noalloc: the projection entry point for callers that cannot allocate
-device memory when they project (graph capture, a memory manager that owns the GPU).
-It must give the same results as fst_project, call after call, using only the
-library's fixed scratch array.  Collected last on purpose (file name)."""
-import numpy as np
+device memory when they project (a process whose memory manager owns all device
+memory after start-up, or a service that must not stall on the allocator).  It must
+give the same results as fst_project, call after call, using only the library's
+fixed scratch array, and refuse work whose scratch does not fit in that array.
+Collected last on purpose (file name)."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -41,3 +42,20 @@ def test_noalloc_matches_fst_project_twice(N, W, eps, dtype):
         assert torch.isfinite(torch.view_as_real(out) if out.is_complex() else out).all()
         err = torch.linalg.vector_norm(out - ref, dim=1) / ynrm
         assert torch.all(err <= tol), err
+
+
+def test_noalloc_rejects_scratch_beyond_the_array():
+    # FP64, N = 2^21 + 1: FFT length 2^23, one pair's intermediate alone is 128 MiB, so the
+    # call must fail with FST_EINVAL before launching anything (the output stays untouched)
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    N = (1 << 21) + 1
+    plan = F.Plan(N, 0.01, eps=1e-3)
+    y = workloads.gaussian(1, N, seed=3).cuda()
+    out = torch.full_like(y, 5.0)
+    with pytest.raises(F.FSTError) as ei:
+        F.fst_project_noalloc(plan.h, y.data_ptr(), out.data_ptr(), 1, N, F.FST_F64, _stream())
+    assert ei.value.status == F.FST_EINVAL
+    assert "fixed scratch" in str(ei.value)
+    torch.cuda.synchronize()
+    assert torch.all(out == 5.0)
