@@ -146,13 +146,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(wl_name, y_sample, W, eps, K, budget_s=10.0):
-    """Oracle fast projection (FP64, numpy/scipy as written) on host cores; returns
-    (samples/s, threads used, sample description)."""
+def cpu_oracle_rate(wl_name, y_sample, plan, budget_s=10.0):
+    """Oracle fast projection (FP64, numpy/scipy as written) on host cores, with its plan
+    prebuilt; returns (samples/s, threads used, sample description)."""
     from oracle import fst_oracle as O
     import numpy as np
     N = y_sample.shape[1]
-    plan = O.make_plan(N, W, K, eps)
     y = np.ascontiguousarray(y_sample.T)
     O.fast_project(plan, y[:, :1])  # warm
     n_done, t0, c0 = 0, time.perf_counter(), time.process_time()
@@ -226,9 +225,15 @@ def run_ragged_bench(args):
     ps = F.PlanSet(params)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
+    # every signal is a view of one contiguous device buffer (one host copy per direction)
+    lens = [N for (N, W, e) in params]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    total = int(offs[-1])
     gen = torch.Generator(device="cuda").manual_seed(3)
-    ys = [torch.randn(N, device="cuda", generator=gen) for (N, W, e) in params]
-    outs = [torch.empty_like(v) for v in ys]
+    yall = torch.randn(total, device="cuda", generator=gen)
+    oall = torch.empty_like(yall)
+    ys = [yall[offs[i]:offs[i + 1]] for i in range(count)]
+    outs = [oall[offs[i]:offs[i + 1]] for i in range(count)]
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ps.project(ys, outs)
@@ -244,7 +249,6 @@ def run_ragged_bench(args):
     launches = F.fst_launch_count() - l0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    total = sum(N for (N, W, e) in params)
     # one fst_project call per signal (each plan's own cached graph)
     def per_signal():
         for h, y, o in zip(ps.h, ys, outs):
@@ -252,12 +256,58 @@ def run_ragged_bench(args):
     for _ in range(2):
         per_signal()
     torch.cuda.synchronize()
+    kp = max(2, args.steps // 4)
     e0.record(stream)
-    for _ in range(max(2, args.steps // 4)):
+    for _ in range(kp):
         per_signal()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_per_signal = e0.elapsed_time(e1) / max(2, args.steps // 4)
+    ms_per_signal = e0.elapsed_time(e1) / kp
+    # end to end: pinned host signals -> device, the ragged projection, results -> host
+    e2e = None
+    if not args.no_e2e:
+        yh = yall.cpu().pin_memory()
+        oh = torch.empty_like(yh).pin_memory()
+
+        def e2e_step():
+            yall.copy_(yh, non_blocking=True)
+            ps.project(ys, outs)
+            oh.copy_(oall, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k2 = max(3, args.steps // 2)
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / k2
+        e2e = {"value": total / wall, "unit": "samples/s", "h2d_bytes_per_step": total * 4,
+               "d2h_bytes_per_step": total * 4, "ms_per_step": wall * 1e3}
+    # every signal against the FP64 oracle would take minutes on the host: a spread sample
+    err, cpu = None, None
+    if not (args.no_err and args.no_cpu):
+        from oracle import fst_oracle as O
+        idx = list(range(0, count, max(1, count // 12)))[:12]
+        oplans = {i: O.make_plan(params[i][0], params[i][1], O.default_K(params[i][0], params[i][1]), params[i][2])
+                  for i in idx}
+        yh64 = {i: ys[i].double().cpu().numpy() for i in idx}
+        if not args.no_err:
+            es = {}
+            for i in idx:
+                ref = O.fast_project(oplans[i], yh64[i])
+                es[str(i)] = float(np.linalg.norm(outs[i].double().cpu().numpy() - ref) / np.linalg.norm(yh64[i]))
+            err = {"max": max(es.values()), "per_signal": es, "tolerance": 1e-5,
+                   "against": "FP64 oracle fast projection with each signal's own plan"}
+        if not args.no_cpu:
+            n_done, c0, t0 = 0, time.process_time(), time.perf_counter()
+            while time.perf_counter() - t0 < 10.0:
+                for i in idx:
+                    O.fast_project(oplans[i], yh64[i])
+                    n_done += params[i][0]
+            wall, cpu_t = time.perf_counter() - t0, time.process_time() - c0
+            cpu = {"value": n_done / wall, "unit": "samples/s", "cores": max(1, round(cpu_t / wall)),
+                   "kind": "oracle", "sample": f"{len(idx)} signals spread over the ragged batch (own plans, "
+                                               f"prebuilt), repeated over {wall:.1f} s"}
     peaks, src = measured_peaks()
     rsum = sum(F.fst_plan_info(h)["r"] for h in ps.h)
     alg = sum(N * 8 + N * F.fst_plan_info(h)["r"] * 4 for h, (N, W, e) in zip(ps.h, params))
@@ -267,13 +317,16 @@ def run_ragged_bench(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["ragged"]["desc"], "signals": count, "samples": total,
                    "mean_r": rsum / count, "plan_many_s": plan_s,
-                   "per_signal_launch_ms": ms_per_signal,
                    "l2": "inputs + outputs + S_T exceed the 129 MB L2; no flush"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "whole ragged step", "peak_source": src},
-        "e2e": None, "cpu_baseline": None, "clocks": clocks,
+        "plan_s": plan_s,
+        "plain": {"ms_per_step": ms_per_signal, "form": "one fst_project call per signal"},
+        "plain_ms_per_step": ms_per_signal, "batched_over_plain": ms_per_signal / ms,
+        "max_rel_err_vs_oracle": err,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
     }
     print(json.dumps(line))
 
@@ -288,6 +341,9 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain one-signal-per-launch arm")
+    ap.add_argument("--no-err", action="store_true", help="skip the per-signal error against the oracle")
+    ap.add_argument("--err-signals", type=int, default=16, help="signals checked against the oracle")
     ap.add_argument("--coeffs", default="auto", choices=["auto", "on", "off"],
                     help="also compute the fast coefficient vector each step (auto: on for c4m)")
     args = ap.parse_args()
@@ -317,7 +373,11 @@ def main():
     y = wl.y.contiguous()
     out = torch.empty_like(y)
     B, N = y.shape
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter()
     plan = F.Plan(N, wl.W, eps=wl.eps)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
     with_coeffs = args.coeffs == "on" or (args.coeffs == "auto" and args.workload == "c4m")
     coef_buf = None
@@ -408,6 +468,59 @@ def main():
     roofline["alu"] = {"achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
                        "flops_per_step": flops, "peak_source": f"{sms} SMs x 128 lanes x 2 x SM max clock"}
 
+    # the plain FP32 form on the same GPU: one fst_project call per signal, generic four-step
+    # kernels with the CUDA-core correction, no graph, no tensor cores (FST_PLAIN=1)
+    plain = None
+    if not args.no_plain:
+        out_plain = torch.empty_like(y)
+        code = F._dtype_code(y.dtype)
+
+        def plain_step():
+            for b in range(B):
+                F.fst_project(plan.h, y[b].data_ptr(), out_plain[b].data_ptr(), 1, N, code, stream.cuda_stream)
+        os.environ["FST_PLAIN"] = "1"
+        try:
+            plain_step()
+            torch.cuda.synchronize()
+            kp = max(2, args.steps // 5)
+            e0.record(stream)
+            for _ in range(kp):
+                plain_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            os.environ.pop("FST_PLAIN", None)
+        plain_ms = max_over_ranks(e0.elapsed_time(e1) / kp, world, "cuda")
+        step()
+        torch.cuda.synchronize()
+        diff = torch.linalg.vector_norm((out_plain - out).reshape(B, -1), dim=1)
+        ynrm = torch.linalg.vector_norm(y.reshape(B, -1), dim=1)
+        plain = {"ms_per_step": plain_ms, "value": job_throughput(B * N, world, plain_ms * 1e-3),
+                 "batched_over_plain": plain_ms / ms,
+                 "max_rel_diff_vs_batched": float((diff / ynrm).max().item()),
+                 "form": "one fst_project per signal; generic FP32 four-step kernels, CUDA-core rank-r "
+                         "correction, no CUDA graph, no tensor cores"}
+
+    # error against the FP64 oracle's fast projection, per signal of a sample (outside the
+    # timed regions); the oracle plan is reused by the CPU baseline below
+    oplan, err = None, None
+    if rank == 0 and not (args.no_err and args.no_cpu):
+        from oracle import fst_oracle as O
+        t0 = time.perf_counter()
+        oplan = O.make_plan(N, wl.W, plan.K, wl.eps)
+        oplan_s = time.perf_counter() - t0
+    if rank == 0 and not args.no_err:
+        nsamp = min(B, args.err_signals)
+        idx = sorted(set(int(round(i * (B - 1) / max(1, nsamp - 1))) for i in range(nsamp)))
+        ys = y[idx].cpu()
+        ys = ys.to(torch.complex128) if ys.is_complex() else ys.double()
+        ref = O.fast_project(oplan, ys.numpy().T).T
+        got = out[idx].cpu().numpy()
+        e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ys.numpy(), axis=1)
+        err = {"max": float(e.max()), "per_signal": {str(i): float(v) for i, v in zip(idx, e)},
+               "tolerance": 1e-5, "against": "FP64 oracle fast projection at the same eps",
+               "oracle_plan_s": oplan_s}
+
     # end to end: pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -444,7 +557,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         ys = y[: min(8, B)].cpu()
         ys = ys.to(torch.complex128) if ys.is_complex() else ys.double()
-        rate, threads, sample = cpu_oracle_rate(args.workload, ys.numpy(), wl.W, wl.eps, plan.K)
+        rate, threads, sample = cpu_oracle_rate(args.workload, ys.numpy(), oplan)
         cpu = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -463,6 +576,11 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "plan_s": plan_s,
+            "plain": plain,
+            "plain_ms_per_step": plain["ms_per_step"] if plain else None,
+            "batched_over_plain": plain["batched_over_plain"] if plain else None,
+            "max_rel_err_vs_oracle": err,
         }
         print(json.dumps(line))
     if world > 1:
