@@ -249,6 +249,7 @@ def run_ragged_bench(args):
     launches = F.fst_launch_count() - l0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    tuning = {f"M=2^{lg}": {"signals_per_group": n, "ms": t} for lg, (n, t) in ps.tuning(ys, outs).items()}
     # one fst_project call per signal (each plan's own cached graph)
     def per_signal():
         for h, y, o in zip(ps.h, ys, outs):
@@ -316,7 +317,7 @@ def run_ragged_bench(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["ragged"]["desc"], "signals": count, "samples": total,
-                   "mean_r": rsum / count, "plan_many_s": plan_s,
+                   "mean_r": rsum / count, "plan_many_s": plan_s, "autotune": tuning,
                    "l2": "inputs + outputs + S_T exceed the 129 MB L2; no flush"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -118,10 +118,12 @@ fst_status fst_plan_export(fst_plan_t plan, int64_t *idx, double *lam, double *D
  *           FST_F64 / FST_C128: the same kernels in FP64.
  * Real signals are processed two at a time as the real and imaginary parts of
  * one complex FFT (B and S_T are real, so they do not mix).
- * FP32: when y is 16-byte aligned and its row stride is a multiple of 16 bytes,
+ * FP32: when y is 16-byte aligned, its row stride is a multiple of 16 bytes and the
+ * batch has more than 32 signal rows (real signals, or two per complex signal),
  * S_T^T y for the whole batch runs on the tensor cores (TF32 with a hi/lo split,
- * three products); other layouts use another kernel with another summation order
- * (same accuracy).  Results are bit-for-bit repeatable for the same call.
+ * three products); smaller batches use FP32 CUDA-core sums, other layouts mma.sync
+ * kernels -- other summation orders, same accuracy.  Results are bit-for-bit
+ * repeatable for the same call.
  * Errors: FST_EINVAL (NULL pointer, batch < 0, ld < N), FST_ENOMEM, FST_ECUDA,
  * FST_ETIMEOUT (see below).
  * Device waits: every wait of the tensor-core kernel on its own copies and products
@@ -236,6 +238,20 @@ fst_status fst_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const
  */
 fst_status fst_project_ragged(const fst_plan_t *plans, const void *const *y, void *const *out,
                               int64_t count, int dtype, void *stream);
+
+/*
+ * fst_ragged_tuning -- the launch grouping the autotuner chose for the four-step signals of
+ * a ragged batch, for the (plans, y, out, dtype) signature of an earlier fst_project_ragged
+ * call: pairs[lg] = signals per launch group of the length class with FFT length 2^lg (0 if
+ * the batch has no four-step signal of that length), ms[lg] (may be NULL) = the measured
+ * device time of that class with the chosen grouping (0 when no timing ran).  Both arrays
+ * have 32 entries.  The first call of a signature times groupings of 16 to 256 MiB of
+ * intermediate per class and keeps the fastest (FST_AUTOTUNE=0 in the environment: 128 MiB,
+ * untimed); the grouping does not change the arithmetic.  Errors: FST_EINVAL (bad
+ * arguments, or no call with this signature).
+ */
+fst_status fst_ragged_tuning(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count,
+                             int dtype, int64_t *pairs, double *ms);
 
 /*
  * fst_sync -- waits for `stream`, then reports the plan's device error word: FST_ETIMEOUT

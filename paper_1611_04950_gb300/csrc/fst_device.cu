@@ -16,6 +16,7 @@
 #include "fst_internal.h"
 #include "../../include/fst_testing.h"
 #include "fst_fast.cuh"
+#include "fst_big.cuh"
 #define FST_TC_KERNELS
 #include "fst_tc.cuh"
 
@@ -302,6 +303,19 @@ static fst_status set_attrs() {
   CU(cudaFuncSetAttribute(k_fastAw<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(32)), "attr");
   CU(cudaFuncSetAttribute(k_fastAw<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(16)), "attr");
   CU(cudaFuncSetAttribute(k_fastAw<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, fastw_smem(8)), "attr");
+  CU(cudaFuncSetAttribute(k_corr_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, cc_smem(64)), "attr");
+  CU(cudaFuncSetAttribute(k_zadd, cudaFuncAttributeMaxDynamicSharedMemorySize, za_smem(64, 1)), "attr");
+  CU(cudaFuncSetAttribute(k_fastB8192, cudaFuncAttributeMaxDynamicSharedMemorySize, fastb8192_smem()), "attr");
+  CU(cudaFuncSetAttribute(k_colA<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(2)), "attr");
+  CU(cudaFuncSetAttribute(k_colA<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(4)), "attr");
+  CU(cudaFuncSetAttribute(k_colA<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(8)), "attr");
+  CU(cudaFuncSetAttribute(k_colA<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(16)), "attr");
+  CU(cudaFuncSetAttribute(k_colA<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(32)), "attr");
+  CU(cudaFuncSetAttribute(k_colC<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(2)), "attr");
+  CU(cudaFuncSetAttribute(k_colC<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(4)), "attr");
+  CU(cudaFuncSetAttribute(k_colC<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(8)), "attr");
+  CU(cudaFuncSetAttribute(k_colC<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(16)), "attr");
+  CU(cudaFuncSetAttribute(k_colC<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(32)), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
   CU(cudaFuncSetAttribute(k_corr_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx), "attr");
@@ -414,9 +428,26 @@ struct DevRunner : Runner {
   ~DevRunner() override {
     for (int i = 0; i < 3; ++i)
       if (cap[i]) cudaStreamDestroy(cap[i]);
-    for (cudaEvent_t e : {fork, join, ev_mid, ev_side, join_side})
+    for (cudaEvent_t e : {fork, join, ev_mid, ev_side, join_side, t0, t1})
       if (e) cudaEventDestroy(e);
     if (tc_err_h) cudaFreeHost(tc_err_h);
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  fst_status timer(int phase, double *ms) override {
+    if (!t0) {
+      CU(cudaEventCreate(&t0), "event");
+      CU(cudaEventCreate(&t1), "event");
+    }
+    if (phase == 0) {
+      CU(cudaEventRecord(t0, cur), "event");
+      return FST_OK;
+    }
+    CU(cudaEventRecord(t1, cur), "event");
+    CU(cudaEventSynchronize(t1), "event sync");
+    float f = 0.f;
+    CU(cudaEventElapsedTime(&f, t0, t1), "elapsed");
+    if (ms) *ms = f;
+    return FST_OK;
   }
   fst_status device_status(bool sync) override {
     if (sync) CU(cudaStreamSynchronize(s), "cudaStreamSynchronize");
@@ -586,12 +617,38 @@ struct DevRunner : Runner {
                           const Layout &L) override { return small_ragged_t(d, count, base, L); }
   fst_status small(const ConvArgs<float> &a, const Layout &L) override { return small_t(a, L); }
   fst_status small(const ConvArgs<double> &a, const Layout &L) override { return small_t(a, L); }
+  template <int P2> fst_status colA_t(const ConvArgs<float> &a, const Layout &L) {
+    TRY(set_attrs());
+    dim3 grid((unsigned)L.ntiles, (unsigned)a.npairs);
+    PROF(P2 == 2 ? "k_colA<2>" : P2 == 4 ? "k_colA<4>" : P2 == 8 ? "k_colA<8>" : P2 == 16 ? "k_colA<16>" : "k_colA<32>",
+         a.npairs, (k_colA<P2><<<grid, 256, big_smem_bytes(P2), cur>>>(a)));
+    LAUNCHED("k_colA");
+    return FST_OK;
+  }
+  template <int P2> fst_status colC_t(const ConvArgs<float> &a, const Layout &L) {
+    TRY(set_attrs());
+    dim3 grid((unsigned)L.ntiles, (unsigned)a.npairs);
+    PROF(P2 == 2 ? "k_colC<2>" : P2 == 4 ? "k_colC<4>" : P2 == 8 ? "k_colC<8>" : P2 == 16 ? "k_colC<16>" : "k_colC<32>",
+         a.npairs, (k_colC<P2><<<grid, 256, big_smem_bytes(P2), cur>>>(a)));
+    LAUNCHED("k_colC");
+    return FST_OK;
+  }
   fst_status passA(const ConvArgs<float> &a, const Layout &L) override {
+    if (L.big) {
+      switch (L.P2) {
+        case 2: return colA_t<2>(a, L);
+        case 4: return colA_t<4>(a, L);
+        case 8: return colA_t<8>(a, L);
+        case 16: return colA_t<16>(a, L);
+        case 32: return colA_t<32>(a, L);
+        default: return fail(FST_EINVAL, "column pass width out of range");
+      }
+    }
     if (!L.fast) return passA_t(a, L);
     const int P = 1 << L.log2P;
     // no fused correction, real signals: 256-byte row loads when the rows allow float2 loads
     // (measured faster for real rows, slower for complex ones)
-    const bool wide_ok = !a.cplx && (uintptr_t)a.y % 8 == 0 && a.ld % 2 == 0;
+    const bool wide_ok = !a.rp && !a.cplx && (uintptr_t)a.y % 8 == 0 && a.ld % 2 == 0;
     if (a.mode != MODE_FULL && wide_ok) {
       TRY(set_attrs());
       const int64_t tiles = ((1 << L.log2Q) / FASTW_NB) * ((a.npairs + FASTW_G - 1) / FASTW_G);
@@ -614,7 +671,14 @@ struct DevRunner : Runner {
   fst_status reduce(const ConvArgs<float> &a, const Layout &L) override { return reduce_t(a, L); }
   fst_status reduce(const ConvArgs<double> &a, const Layout &L) override { return reduce_t(a, L); }
   fst_status passB(const ConvArgs<float> &a, const Layout &L) override {
-    if (!L.fast || L.log2Q != 12) return passB_t(a, L);
+    if ((L.fast || L.big) && L.log2Q == 13 && a.tw8) {
+      TRY(set_attrs());
+      dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
+      PROF("k_fastB8192", a.npairs, (k_fastB8192<<<grid, 512, fastb8192_smem(), cur>>>(a, a.tw8)));
+      LAUNCHED("k_fastB8192");
+      return FST_OK;
+    }
+    if (!(L.fast || L.big) || L.log2Q != 12) return passB_t(a, L);
     dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
     PROF("k_fastB4096", a.npairs, (k_fastB4096<<<grid, 256, 0, cur>>>(a)));
     LAUNCHED("k_fastB4096");
@@ -683,6 +747,39 @@ struct DevRunner : Runner {
     LAUNCHED("k_corr_tc");
     return FST_OK;
   }
+  fst_status rcorr(const RSig *sigs, int nsig, const RItem *items, int nitems, int cplx, float *part,
+                   float *acoef) override {
+    if (nitems <= 0) return FST_OK;
+    PROF("k_rcorr_part", nitems, (k_rcorr_part<<<(unsigned)nitems, 256, 0, cur>>>(sigs, items, cplx, part)));
+    LAUNCHED("k_rcorr_part");
+    PROF("k_rcorr_reduce", nsig, (k_rcorr_reduce<<<(unsigned)nsig, 128, 0, cur>>>(sigs, part, acoef)));
+    LAUNCHED("k_rcorr_reduce");
+    return FST_OK;
+  }
+  fst_status rzadd(const RSig *sigs, const RItem *items, int nitems, int cplx, const float *acoef) override {
+    if (nitems <= 0) return FST_OK;
+    PROF("k_rzadd", nitems, (k_rzadd<<<(unsigned)nitems, 256, 0, cur>>>(sigs, items, cplx, acoef)));
+    LAUNCHED("k_rzadd");
+    return FST_OK;
+  }
+  fst_status corr_cc(const ConvArgs<float> &a) override {
+    TRY(set_attrs());
+    PROF("k_corr_cc", a.npairs,
+         (k_corr_cc<<<(unsigned)((a.N + CORR_BLOCK - 1) / CORR_BLOCK), CC_THREADS, cc_smem(a.rpad), cur>>>(a)));
+    LAUNCHED("k_corr_cc");
+    return FST_OK;
+  }
+  fst_status zadd(const ConvArgs<float> &a) override {
+    TRY(set_attrs());
+    const int64_t rows = a.cplx ? 2 * a.batch : a.batch;
+    const int ng = za_groups(rows), ns = ZA_THREADS / ng;
+    const int64_t nrb = (rows + ng * ZA_RG - 1) / (ng * ZA_RG);
+    const int64_t blocks = nrb * ((a.N + ns - 1) / ns);
+    if (blocks >= (1LL << 31)) return fail(FST_EINVAL, "batch too large for the correction pass");
+    PROF("k_zadd", a.npairs, (k_zadd<<<(unsigned)blocks, ZA_THREADS, za_smem(a.rpad, ng), cur>>>(a)));
+    LAUNCHED("k_zadd");
+    return FST_OK;
+  }
   fst_status z_rmw(const ConvArgs<float> &a, const float *ST) override {
     const int nsig = a.cplx ? ZR_ROWS / 2 : ZR_ROWS;
     dim3 grid((unsigned)((a.N + ZR_N - 1) / ZR_N), (unsigned)((a.batch + nsig - 1) / nsig));
@@ -705,6 +802,16 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   fst_status passC(const ConvArgs<float> &a, const Layout &L) override {
+    if (L.big) {
+      switch (L.P2) {
+        case 2: return colC_t<2>(a, L);
+        case 4: return colC_t<4>(a, L);
+        case 8: return colC_t<8>(a, L);
+        case 16: return colC_t<16>(a, L);
+        case 32: return colC_t<32>(a, L);
+        default: return fail(FST_EINVAL, "column pass width out of range");
+      }
+    }
     if (!L.fast) return passC_t(a, L);
     FastArgs f{a, a.ST_hl};
     dim3 grid((unsigned)L.ntiles, (unsigned)((a.npairs + FAST_G - 1) / FAST_G));
@@ -1081,7 +1188,7 @@ struct RaggedCtx {
   std::vector<const void *> sig;
   std::vector<fst_plan_t> plans;   // the batch's plans, in call order
   std::vector<uint64_t> gens;      // their workspace generations when the graph was recorded
-  std::vector<void *> bufs;        // descriptor arrays (cudaMalloc), owned by the context
+  fst::RaggedState state;          // descriptor arrays and workspaces (cudaMalloc), launch choices
   cudaGraphExec_t exec = nullptr;
   long long nodes = 0;
   int seen = 0;
@@ -1092,7 +1199,7 @@ std::vector<RaggedCtx *> g_ragged;
 void free_ctx(RaggedCtx *c) {
   cudaDeviceSynchronize();
   if (c->exec) cudaGraphExecDestroy(c->exec);
-  for (void *b : c->bufs) cudaFree(b);
+  for (void *b : c->state.bufs) cudaFree(b);
   delete c;
 }
 bool ctx_current(const RaggedCtx *c) {
@@ -1114,9 +1221,9 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
   for (int64_t i = 0; i < count; ++i)
     if (!plans[i]) return fail(FST_EINVAL, "NULL plan");
   if (!plans[0]->R->device()) {
-    std::vector<void *> bufs;
-    fst_status st = run_ragged(plans, y, out, count, dtype, bufs);
-    for (void *b : bufs) plans[0]->R->release(b);
+    RaggedState rs;
+    fst_status st = run_ragged(plans, y, out, count, dtype, rs);
+    for (void *b : rs.bufs) plans[0]->R->release(b);
     return st;
   }
   std::lock_guard<std::recursive_mutex> lk(g_ragged_mu);
@@ -1163,14 +1270,14 @@ extern "C" fst_status fst_project_ragged(const fst_plan_t *plans, const void *co
   for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream(stream);
   if (ctx->seen == 0 || !graphs) {
     ctx->seen = 1;
-    return run_ragged(plans, y, out, count, dtype, ctx->bufs);
+    return run_ragged(plans, y, out, count, dtype, ctx->state);
   }
   // second call: record the batch into a graph on a private stream
   if (!g_ragged_cap) CU(cudaStreamCreateWithFlags(&g_ragged_cap, cudaStreamNonBlocking), "stream");
   for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream((void *)g_ragged_cap);
   const long long l0 = g_launches;
   CU(cudaStreamBeginCapture(g_ragged_cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-  fst_status st = run_ragged(plans, y, out, count, dtype, ctx->bufs);
+  fst_status st = run_ragged(plans, y, out, count, dtype, ctx->state);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(g_ragged_cap, &g);
   for (int64_t i = 0; i < count; ++i) plans[i]->R->set_stream(stream);
@@ -1207,6 +1314,29 @@ void forget_ragged(fst_plan_t p) {
   }
 }
 }  // namespace fst
+
+extern "C" fst_status fst_ragged_tuning(const fst_plan_t *plans, const void *const *y, void *const *out,
+                                        int64_t count, int dtype, int64_t *pairs, double *ms) {
+  if (count <= 0 || !plans || !y || !out || !pairs) return fail(FST_EINVAL, "bad arguments");
+  std::lock_guard<std::recursive_mutex> lk(g_ragged_mu);
+  std::vector<const void *> sig;
+  sig.reserve(3 * count + 1);
+  sig.push_back((const void *)(intptr_t)dtype);
+  for (int64_t i = 0; i < count; ++i) {
+    sig.push_back(plans[i]);
+    sig.push_back(y[i]);
+    sig.push_back(out[i]);
+  }
+  for (RaggedCtx *c : g_ragged)
+    if (c->sig == sig) {
+      for (int lg = 0; lg < 32; ++lg) {
+        pairs[lg] = lg < (int)c->state.chunk.size() ? c->state.chunk[lg] : 0;
+        if (ms) ms[lg] = lg < (int)c->state.tune_ms.size() ? c->state.tune_ms[lg] : 0.0;
+      }
+      return FST_OK;
+    }
+  return fail(FST_EINVAL, "no ragged call with this signature has run");
+}
 
 extern "C" fst_status fst_test_tc_stall(int launches, double limit_s) {
   if (launches < 0 || !(limit_s > 0.0) || limit_s > 2.0) return fail(FST_EINVAL, "bad stall request");

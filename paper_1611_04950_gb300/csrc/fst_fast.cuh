@@ -56,6 +56,12 @@ __device__ __forceinline__ void mma3(float *d, const uint32_t *ahi, const uint32
 
 // In-register DFT of length P (8, 16 or 32) in natural order, unnormalised.
 template <int P, bool INV> struct RegDft;
+template <bool INV> struct RegDft<2, INV> {
+  __device__ __forceinline__ static void run(float2 *v) { Dft<float, 2, INV>::run(v); }
+};
+template <bool INV> struct RegDft<4, INV> {
+  __device__ __forceinline__ static void run(float2 *v) { Dft<float, 4, INV>::run(v); }
+};
 template <bool INV> struct RegDft<8, INV> {
   __device__ __forceinline__ static void run(float2 *v) { Dft<float, 8, INV>::run(v); }
 };
@@ -140,13 +146,13 @@ template <int P> __device__ __forceinline__ void idft_half_out(const float2 *v, 
 
 // P-point DFT of column n2 (v; rows n1 >= P/2 zero), times W_M^{n2 k1}, stored to
 // inter[row0 + k1 Q + n2].
-// k1 = 8h + b, W^{k1} = W^{8h} W^b: table lookups for W, W^8, W^16, small powers by at most
-// two products, applied and stored right away.
 template <int P>
 __device__ __forceinline__ void fastA_finish(const ConvArgs<float> &a, float2 *v, int64_t row0, int64_t n2) {
   const int Q = 1 << a.log2Q;
   dft_half_in<P>(v);
   float2 *dst = a.inter + row0 + n2;
+  // k1 = 8h + b, W^{k1} = W^{8h} W^b: table lookups for W, W^8, W^16, small powers by at most
+  // two products, each factor applied and stored right away
   const float2 w1 = a.tw.root<false>((uint64_t)n2, a.log2M);
   const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
   float2 wh[4];
@@ -188,6 +194,10 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, int src
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int P>
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
     for (int t = 0; t < 16; ++t) row[j + T * t] = x[t];
     return;
   }
-  const float *sp = a.spec + (int64_t)k1 * Q;
+  const float *sp = spec_of(a, pl) + (int64_t)k1 * Q;
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = cscale(x[t], __ldg(sp + j + T * t));
   // inverse stage 1: its inputs x[j + 256 t] are already in registers
@@ -434,6 +444,121 @@ __global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
     else wt = cmul(wt, wstep);
   }
 }
+
+// ---------------------------------------------------------------------------
+// pass B for Q = 8192 = 16^3 x 2 (512 threads, 16 values per thread), no fused reduce
+// grid (P, npairs).  Stockham stages (radix R at sub-length Ns, butterfly j reads
+// x[j + t Q/R], twiddles by W_{Ns R}^{(j mod Ns) t}, writes y[(j/Ns) Ns R + j mod Ns + t Ns]):
+//   forward  R16 Ns=1 (from global), R16 Ns=16, R16 Ns=256, R2 Ns=4096 (natural order out,
+//            8 butterflies per thread at j = tid + 512 q: values at j and j + 4096)
+//   spectrum in registers
+//   inverse  R2 Ns=1 (same positions), R16 Ns=2, R16 Ns=32, R16 Ns=512 (natural order out)
+// tw8: W_8192^j (j < 4096), then [t][k] W_32^{k t} (k < 2), [t][k] W_512^{k t} (k < 32),
+//      [t][k] W_8192^{k t} (k < 512), t < 16
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(512, 2) k_fastB8192(const ConvArgs<float> a, const float2 *tw8) {
+  constexpr int Q = 8192, T = 512;
+  extern __shared__ __align__(16) float2 buf8[];
+  const int P = 1 << a.log2P;
+  const int k1 = blockIdx.x;
+  const int64_t pl = blockIdx.y;
+  float2 *row = a.inter + (pl * P + k1) * (int64_t)Q;
+  const int j = threadIdx.x;
+  float2 x[16];
+  // forward stage 1 (R16, Ns = 1): inputs x[j + 512 t] from global
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = row[j + T * t];
+  Dft<float, 16, false>::run(x);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf8[pad(16 * j + t)] = x[t];
+  __syncthreads();
+  // stage 2 (R16, Ns = 16)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf8[pad(j + T * t)];
+  tw_table16(a.twB, 16, j & 15, false, x);
+  Dft<float, 16, false>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf8[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
+  __syncthreads();
+  // stage 3 (R16, Ns = 256)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf8[pad(j + T * t)];
+  tw_table16(a.twB + 256, 256, j & 255, false, x);
+  Dft<float, 16, false>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf8[pad(((j >> 8) << 12) + (j & 255) + 256 * t)] = x[t];
+  __syncthreads();
+  // stage 4 (R2, Ns = 4096): butterflies jq = j + 512 q, values at jq (x[2q]) and jq + 4096 (x[2q+1])
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int jq = j + T * q;
+    const float2 u0 = buf8[pad(jq)];
+    const float2 u1 = cmul(buf8[pad(jq + 4096)], __ldg(tw8 + TW8_R2 + jq));
+    x[2 * q] = cadd(u0, u1);
+    x[2 * q + 1] = csub(u0, u1);
+  }
+  if (a.mode == MODE_FORWARD) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      row[j + T * q] = x[2 * q];
+      row[j + T * q + 4096] = x[2 * q + 1];
+    }
+    return;
+  }
+  const float *sp = spec_of(a, pl) + (int64_t)k1 * Q;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    x[2 * q] = cscale(x[2 * q], __ldg(sp + j + T * q));
+    x[2 * q + 1] = cscale(x[2 * q + 1], __ldg(sp + j + T * q + 4096));
+  }
+  // inverse stage 1 (R2, Ns = 1): butterflies jq read x[jq], x[jq + 4096] (in registers) and
+  // write y[2 jq], y[2 jq + 1]
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int jq = j + T * q;
+    buf8[pad(2 * jq)] = cadd(x[2 * q], x[2 * q + 1]);
+    buf8[pad(2 * jq + 1)] = csub(x[2 * q], x[2 * q + 1]);
+  }
+  __syncthreads();
+  // inverse stage 2 (R16, Ns = 2)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf8[pad(j + T * t)];
+  tw_table16(tw8 + TW8_32, 2, j & 1, true, x);
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf8[pad(((j >> 1) << 5) + (j & 1) + 2 * t)] = x[t];
+  __syncthreads();
+  // inverse stage 3 (R16, Ns = 32)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf8[pad(j + T * t)];
+  tw_table16(tw8 + TW8_512, 32, j & 31, true, x);
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf8[pad(((j >> 5) << 9) + (j & 31) + 32 * t)] = x[t];
+  __syncthreads();
+  // inverse stage 4 (R16, Ns = 512): outputs at j + 512 t = natural n2
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf8[pad(j + T * t)];
+  tw_table16(tw8 + TW8_8192, 512, j, true, x);
+  Dft<float, 16, true>::run(x);
+  // times W_M^{-n2 k1}, n2 = j + 512 t, straight to global memory
+  const float2 wj = a.tw.root<true>((uint64_t)j * (uint64_t)k1, a.log2M);
+  const float2 wstep = a.tw.root<true>((uint64_t)T * (uint64_t)k1, a.log2M);
+  float2 wt = wj;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    row[j + T * t] = cmul(x[t], wt);
+    if (t == 7) wt = cmul(wj, a.tw.root<true>((uint64_t)(8 * T) * (uint64_t)k1, a.log2M));
+    else wt = cmul(wt, wstep);
+  }
+}
+__host__ __device__ constexpr int fastb8192_smem() { return padded_size(8192) * 8; }
 
 // ---------------------------------------------------------------------------
 // pass C: load columns, inverse P-point DFT, correction epilogue (tensor cores), store
@@ -732,6 +857,330 @@ __global__ void __launch_bounds__(ZR_THREADS) k_z_rmw(const ConvArgs<float> a, c
       v.x += zr;
       v.y += zi;
       *o = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// out += S_T a over the whole batch on CUDA cores (rpad <= 64): a block of ZA_THREADS threads
+// takes ns = ZA_THREADS / ng samples and up to 16 ng signal rows (ng = ceil(rows / 16), at
+// most 8: real signals, or the (re, im) rows of complex ones; row b of a is acoef row b).  The
+// block's S_T rows are staged once in shared memory, [sample][j] with a 16-byte aligned odd
+// stride (conflict-free float4 reads), and its a rows transposed to [j][row] (float4
+// broadcasts).  Thread (sample i, row group g) keeps ZA_RG sums in registers: per 4 j, one
+// float4 of S and ZA_RG / 4 float4 of a feed 4 ZA_RG FMAs.  Then the sums are added into out
+// (coalesced along the samples).
+// 1-D grid of ceil(N / ns) x (row blocks) blocks, block b = sample block b / nrb, row block
+// b % nrb: the row blocks of the same samples run side by side, so their S_T rows come from L2.
+// ---------------------------------------------------------------------------
+constexpr int ZA_THREADS = 256, ZA_RG = 16, ZA_ROWS = 128;
+// row groups per block: ceil(rows / 16) rounded up to a power of two, at most 8, so that
+// ZA_THREADS / ng samples times ng groups is exactly the block
+__host__ __device__ inline int za_groups(int64_t rows) {
+  int g = 1;
+  while (g < ZA_ROWS / ZA_RG && (int64_t)g * ZA_RG < rows) g *= 2;
+  return g;
+}
+__host__ __device__ inline int za_smem(int rpad, int ng) {
+  return ((ZA_THREADS / ng) * (rpad + 4) + rpad * (ng * ZA_RG + 4)) * 4;
+}
+
+__global__ void __launch_bounds__(ZA_THREADS) k_zadd(const ConvArgs<float> a) {
+  extern __shared__ __align__(16) float zsm[];
+  const int rpad = a.rpad, sst = rpad + 4;
+  const int64_t rows = a.cplx ? 2 * a.batch : a.batch;
+  const int ng = za_groups(rows), ns = ZA_THREADS / ng, brows = ng * ZA_RG, ast = brows + 4;
+  float *st = zsm;                        // [ns][sst]
+  float *as = zsm + ns * sst;             // [rpad][ast]
+  const int64_t nrb = (rows + brows - 1) / brows;
+  const int64_t row0 = ((int64_t)blockIdx.x % nrb) * brows;
+  const int nrow = (int)(rows - row0 < brows ? rows - row0 : brows);
+  const int64_t n0 = ((int64_t)blockIdx.x / nrb) * ns;
+  // S_T rows n0 .. n0 + ns - 1 (zero past N)
+  for (int e = threadIdx.x; e < ns * (rpad / 4); e += ZA_THREADS) {
+    const int i = e / (rpad / 4), q = e % (rpad / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n0 + i < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.ST + (n0 + i) * rpad) + q);
+    *reinterpret_cast<float4 *>(st + i * sst + 4 * q) = v;
+  }
+  // a rows of this block, transposed: as[j][row]
+  for (int e = threadIdx.x; e < rpad * brows; e += ZA_THREADS) {
+    const int rr = e / rpad, j = e % rpad;
+    as[j * ast + rr] = (rr < nrow && j < a.r) ? a.acoef[(row0 + rr) * rpad + j] : 0.f;
+  }
+  __syncthreads();
+  const int i = threadIdx.x % ns, g = threadIdx.x / ns;
+  const int64_t n = n0 + i;
+  float acc[ZA_RG];
+#pragma unroll
+  for (int q = 0; q < ZA_RG; ++q) acc[q] = 0.f;
+  const float *srow = st + i * sst;
+  const float *acol = as + g * ZA_RG;
+  for (int j = 0; j < rpad; j += 4) {
+    const float4 s4 = *reinterpret_cast<const float4 *>(srow + j);
+#pragma unroll
+    for (int q = 0; q < ZA_RG; q += 4) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(acol + (j + 0) * ast + q);
+      const float4 a1 = *reinterpret_cast<const float4 *>(acol + (j + 1) * ast + q);
+      const float4 a2 = *reinterpret_cast<const float4 *>(acol + (j + 2) * ast + q);
+      const float4 a3 = *reinterpret_cast<const float4 *>(acol + (j + 3) * ast + q);
+      acc[q + 0] = fmaf(s4.w, a3.x, fmaf(s4.z, a2.x, fmaf(s4.y, a1.x, fmaf(s4.x, a0.x, acc[q + 0]))));
+      acc[q + 1] = fmaf(s4.w, a3.y, fmaf(s4.z, a2.y, fmaf(s4.y, a1.y, fmaf(s4.x, a0.y, acc[q + 1]))));
+      acc[q + 2] = fmaf(s4.w, a3.z, fmaf(s4.z, a2.z, fmaf(s4.y, a1.z, fmaf(s4.x, a0.z, acc[q + 2]))));
+      acc[q + 3] = fmaf(s4.w, a3.w, fmaf(s4.z, a2.w, fmaf(s4.y, a1.w, fmaf(s4.x, a0.w, acc[q + 3]))));
+    }
+  }
+  if (n >= a.N) return;
+  if (!a.cplx) {
+#pragma unroll
+    for (int q = 0; q < ZA_RG; ++q) {
+      const int rr = g * ZA_RG + q;
+      if (rr < nrow) a.out[(row0 + rr) * a.ld + n] += acc[q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < ZA_RG; q += 2) {
+      const int rr = g * ZA_RG + q;
+      if (rr < nrow) {
+        float2 *o = reinterpret_cast<float2 *>(a.out) + ((row0 + rr) >> 1) * a.ld + n;
+        float2 v = *o;
+        v.x += acc[q];
+        v.y += acc[q + 1];
+        *o = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S_T^T y for small batches (at most CC_ROWS signal rows: real signals, or the (re, im) rows
+// of complex ones) on CUDA cores, in FP32: the MMA tile of the tensor-core kernel would be
+// mostly empty there and each k-tile's fixed cost dominates.  A block takes CORR_BLOCK
+// samples in sub-chunks of CC_SUB; y (transposed to [sample][row]) and S_T ([sample][j]) of
+// a sub-chunk are staged in shared memory.  Thread (row group of 4, j group of 8, sample
+// slice s) keeps 32 sums; per sample one float4 of y and two of S feed 32 FMAs.  The slices
+// are summed in a fixed order at the end and one partial per (pair, block, part, j) is
+// written, the layout k_corr_reduce reads (nkb = ceil(N / CORR_BLOCK)).
+// grid ceil(N / CORR_BLOCK), CC_THREADS threads, dynamic shared memory cc_smem(rpad).
+// ---------------------------------------------------------------------------
+constexpr int CC_ROWS = 32, CC_SUB = 128, CC_THREADS = 256;
+// staging area: y [CC_SUB][CC_ROWS + 4] and S_T [CC_SUB][rpad + 4]; at the end it holds the
+// slice sums [CC_THREADS][33]
+__host__ __device__ constexpr int cc_smem(int rpad) {
+  return ((CC_SUB * (CC_ROWS + 4) + CC_SUB * (rpad + 4)) > CC_THREADS * 33
+              ? (CC_SUB * (CC_ROWS + 4) + CC_SUB * (rpad + 4))
+              : CC_THREADS * 33) * 4;
+}
+
+__global__ void __launch_bounds__(CC_THREADS) k_corr_cc(const ConvArgs<float> a) {
+  extern __shared__ __align__(16) float csm2[];
+  const int rpad = a.rpad, sst = rpad + 4;
+  constexpr int YST = CC_ROWS + 4;
+  float *yt = csm2;                     // [CC_SUB][YST]
+  float *st = csm2 + CC_SUB * YST;      // [CC_SUB][sst]
+  const int rows = (int)(a.cplx ? 2 * a.batch : a.batch);
+  const int nrg = (rows + 3) / 4, njg = rpad / 8;
+  const int combos = nrg * njg;
+  const int nslice = CC_THREADS / combos;            // host guarantees combos <= CC_THREADS
+  const int tid = threadIdx.x;
+  const int combo = tid % combos, slice = tid / combos;
+  const bool active = slice < nslice;
+  const int rg = combo % nrg, jg = combo / nrg;
+  const int64_t blk = blockIdx.x;
+  float acc[4][8];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  for (int sub = 0; sub < CORR_BLOCK / CC_SUB; ++sub) {
+    const int64_t n0 = blk * CORR_BLOCK + (int64_t)sub * CC_SUB;
+    if (n0 >= a.N) break;
+    __syncthreads();
+    // S_T rows by cp.async (zero past N), y rows (the 4 nrg rows used; zero past N and past the
+    // last row) transposed through registers meanwhile
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(st);
+    for (int e = tid; e < CC_SUB * (rpad / 4); e += CC_THREADS) {
+      const int i = e / (rpad / 4), q = e % (rpad / 4);
+      const bool ok = n0 + i < a.N;
+      cp_async16(sbase + (uint32_t)((i * sst + 4 * q) * 4), ok ? a.ST + (n0 + i) * rpad + 4 * q : a.ST, ok ? 16 : 0);
+    }
+    cp_async_commit();
+    for (int e = tid; e < 4 * nrg * CC_SUB; e += CC_THREADS) {
+      const int row = e / CC_SUB, i = e % CC_SUB;
+      const int64_t n = n0 + i;
+      float v = 0.f;
+      if (row < rows && n < a.N) {
+        if (!a.cplx) v = a.y[(int64_t)row * a.ld + n];
+        else v = a.y[((int64_t)(row >> 1) * a.ld + n) * 2 + (row & 1)];
+      }
+      yt[i * YST + row] = v;
+    }
+    cp_async_wait0();
+    __syncthreads();
+    if (active) {
+      for (int i = slice; i < CC_SUB; i += nslice) {
+        const float4 y4 = *reinterpret_cast<const float4 *>(yt + i * YST + 4 * rg);
+        const float4 s0 = *reinterpret_cast<const float4 *>(st + i * sst + 8 * jg);
+        const float4 s1 = *reinterpret_cast<const float4 *>(st + i * sst + 8 * jg + 4);
+        const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+        const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(yv[u], sv[v], acc[u][v]);
+      }
+    }
+  }
+  // sum the slices in a fixed order: red[slice][combo][32] over the staging area
+  __syncthreads();
+  float *red = csm2;
+  if (active) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) red[(slice * combos + combo) * 33 + u * 8 + v] = acc[u][v];
+  }
+  __syncthreads();
+  const int nK = (int)((a.N + CORR_BLOCK - 1) / CORR_BLOCK);
+  for (int e = tid; e < combos * 32; e += CC_THREADS) {
+    const int cb = e / 32, w = e % 32, u = w / 8, v = w % 8;
+    float sum = 0.f;
+    for (int sl = 0; sl < nslice; ++sl) sum += red[(sl * combos + cb) * 33 + w];
+    const int row = (cb % nrg) * 4 + u, j = (cb / nrg) * 8 + v;
+    if (row < rows && j < rpad) {
+      // row -> (pair, part): real signal row = 2 pair + part; complex row = 2 signal + part
+      const int64_t pair = row >> 1;
+      const int comp = row & 1;
+      a.part[((pair * nK + blk) * 2 + comp) * rpad + j] = sum;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rank-r correction of a ragged batch, one plan per signal (FP32, CUDA cores).  Every Slepian
+// vector is symmetric or antisymmetric, s_l(N-1-n) = (-1)^l s_l(n) (B commutes with the
+// exchange J), so only the rows n < H = ceil(N/2) of S_T are read, halving its traffic:
+//   c_j = sum_{n<H} s_j(n) (y(n) +- y(N-1-n))   (the middle sample of an odd N once)
+//   z(n) = z+(n) + z-(n),  z(N-1-n) = z+(n) - z-(n),  z+- = sums over the (anti)symmetric j
+//   k_rcorr_part   item (signal, chunk of CORR_BLOCK of the H folded samples): partial c, the
+//                  8 warps split the samples, lanes split j (coalesced S_T rows), fixed order
+//   k_rcorr_reduce block per signal: a = D o (sum of its partials in chunk order)
+//   k_rzadd        item: out(n) and out(N-1-n) += ... for the chunk's n (thread per n)
+// acoef: [signal][2][RC_RMAX]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool rs_odd(const RSig &q, int j) { return (q.odd[j >> 5] >> (j & 31)) & 1u; }
+
+__global__ void __launch_bounds__(256) k_rcorr_part(const RSig *sigs, const RItem *items, int cplx, float *part) {
+  __shared__ float red[8][4][32];
+  const RItem it = items[blockIdx.x];
+  const RSig q = sigs[it.sig];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t H = (q.N + 1) / 2;
+  const int64_t n0 = (int64_t)it.chunk * CORR_BLOCK;
+  const int64_t nend = (H - n0 < CORR_BLOCK) ? H : n0 + CORR_BLOCK;
+  for (int j0 = 0; j0 < q.rpad; j0 += 64) {
+    const int ja = j0 + lane, jb = j0 + 32 + lane;
+    const bool oa = rs_odd(q, ja & (RC_RMAX - 1)), ob = rs_odd(q, jb & (RC_RMAX - 1));
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t n = n0 + w; n < nend; n += 8) {
+      const int64_t m = q.N - 1 - n;
+      float yr, yi = 0.f, mr = 0.f, mi = 0.f;
+      if (cplx) {
+        const float2 v = reinterpret_cast<const float2 *>(q.y)[n];
+        yr = v.x;
+        yi = v.y;
+        if (m != n) {
+          const float2 u = reinterpret_cast<const float2 *>(q.y)[m];
+          mr = u.x;
+          mi = u.y;
+        }
+      } else {
+        yr = q.y[n];
+        if (m != n) mr = q.y[m];
+      }
+      const float *row = q.ST + n * q.rpad;
+      const float sa = ja < q.rpad ? __ldg(row + ja) : 0.f;
+      const float sb = jb < q.rpad ? __ldg(row + jb) : 0.f;
+      acc[0] = fmaf(sa, oa ? yr - mr : yr + mr, acc[0]);
+      acc[1] = fmaf(sa, oa ? yi - mi : yi + mi, acc[1]);
+      acc[2] = fmaf(sb, ob ? yr - mr : yr + mr, acc[2]);
+      acc[3] = fmaf(sb, ob ? yi - mi : yi + mi, acc[3]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[w][u][lane] = acc[u];
+    __syncthreads();
+    if (threadIdx.x < 128) {
+      const int comp = threadIdx.x >> 6, jj = threadIdx.x & 63;   // jj < 32: ja; else jb
+      const int u = (jj < 32 ? 0 : 2) + comp, l = jj & 31;
+      float sum = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) sum += red[ww][u][l];
+      const int j = j0 + jj;
+      if (j < q.rpad) part[q.part + ((int64_t)it.chunk * 2 + comp) * q.rpad + j] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_rcorr_reduce(const RSig *sigs, const float *part, float *acoef) {
+  const RSig q = sigs[blockIdx.x];
+  for (int t = threadIdx.x; t < 2 * q.rpad; t += blockDim.x) {
+    const int comp = t / q.rpad, j = t % q.rpad;
+    float sum = 0.f;
+    for (int c = 0; c < q.nK; ++c) sum += part[q.part + ((int64_t)c * 2 + comp) * q.rpad + j];
+    acoef[((int64_t)blockIdx.x * 2 + comp) * RC_RMAX + j] = j < q.r ? __ldg(q.D + j) * sum : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rzadd(const RSig *sigs, const RItem *items, int cplx, const float *acoef) {
+  // a split by parity: as[c][0][j] = a_j for symmetric j (else 0), as[c][1][j] for antisymmetric
+  __shared__ __align__(16) float as[2][2][RC_RMAX];
+  const RItem it = items[blockIdx.x];
+  const RSig q = sigs[it.sig];
+  for (int t = threadIdx.x; t < 2 * RC_RMAX; t += blockDim.x) {
+    const int c = t / RC_RMAX, j = t % RC_RMAX;
+    const float v = acoef[((int64_t)it.sig * 2) * RC_RMAX + t];
+    const bool o = rs_odd(q, j);
+    as[c][0][j] = o ? 0.f : v;
+    as[c][1][j] = o ? v : 0.f;
+  }
+  __syncthreads();
+  const int64_t H = (q.N + 1) / 2;
+  const int64_t n0 = (int64_t)it.chunk * CORR_BLOCK;
+  for (int i = threadIdx.x; i < CORR_BLOCK; i += blockDim.x) {
+    const int64_t n = n0 + i;
+    if (n >= H) break;
+    const int64_t m = q.N - 1 - n;
+    const float4 *row = reinterpret_cast<const float4 *>(q.ST + n * q.rpad);
+    float zp = 0.f, zm = 0.f, wp = 0.f, wm = 0.f;   // re (z) and im (w), symmetric / antisymmetric
+    for (int j4 = 0; j4 < q.rpad / 4; ++j4) {
+      const float4 s4 = __ldg(row + j4);
+      const float4 ap = *reinterpret_cast<const float4 *>(&as[0][0][4 * j4]);
+      const float4 am = *reinterpret_cast<const float4 *>(&as[0][1][4 * j4]);
+      zp = fmaf(s4.w, ap.w, fmaf(s4.z, ap.z, fmaf(s4.y, ap.y, fmaf(s4.x, ap.x, zp))));
+      zm = fmaf(s4.w, am.w, fmaf(s4.z, am.z, fmaf(s4.y, am.y, fmaf(s4.x, am.x, zm))));
+      if (cplx) {
+        const float4 bp = *reinterpret_cast<const float4 *>(&as[1][0][4 * j4]);
+        const float4 bm = *reinterpret_cast<const float4 *>(&as[1][1][4 * j4]);
+        wp = fmaf(s4.w, bp.w, fmaf(s4.z, bp.z, fmaf(s4.y, bp.y, fmaf(s4.x, bp.x, wp))));
+        wm = fmaf(s4.w, bm.w, fmaf(s4.z, bm.z, fmaf(s4.y, bm.y, fmaf(s4.x, bm.x, wm))));
+      }
+    }
+    if (cplx) {
+      float2 *o = reinterpret_cast<float2 *>(q.out);
+      float2 v = o[n];
+      v.x += zp + zm;
+      v.y += wp + wm;
+      o[n] = v;
+      if (m != n) {
+        float2 u = o[m];
+        u.x += zp - zm;
+        u.y += wp - wm;
+        o[m] = u;
+      }
+    } else {
+      q.out[n] += zp + zm;
+      if (m != n) q.out[m] += zp - zm;
     }
   }
 }

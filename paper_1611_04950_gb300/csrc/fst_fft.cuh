@@ -143,7 +143,9 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
 #pragma unroll
     for (int b = 1; b < 4; ++b)
 #pragma unroll
-      for (int c = 1; c < 4; ++c) v[4 * c + b] = cmul(v[4 * c + b], wconst<T, 16, INV>(b * c));
+      for (int c = 1; c < 4; ++c)
+        // W_16^4 = -i (conjugated: +i) is a swap and a sign, not a product
+        v[4 * c + b] = (b * c == 4) ? mul_mi<INV>(v[4 * c + b]) : cmul(v[4 * c + b], wconst<T, 16, INV>(b * c));
     c2<T> o[16];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

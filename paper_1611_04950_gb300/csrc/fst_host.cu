@@ -65,8 +65,12 @@ Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast) {
     return L;
   }
   L.small = false;
-  const int qmax = dbl ? 13 : 14, qmin = dbl ? 11 : 12;
-  L.log2Q = std::min(qmax, std::max(qmin, log2M - 5));
+  if (dbl) {
+    L.log2Q = std::min(13, std::max(11, log2M - 5));
+  } else {
+    // FP32: 4096-point rows up to M = 2^22 (P <= 1024), then P = 1024 with longer rows
+    L.log2Q = log2M <= 22 ? 12 : log2M - 10;
+  }
   L.log2P = log2M - L.log2Q;
   const int P = 1 << L.log2P, Q = 1 << L.log2Q;
   L.Pnz = (int)((N + Q - 1) / Q);
@@ -81,6 +85,17 @@ Layout make_layout(int64_t N, int log2M, bool dbl, int rpad, bool allow_fast) {
     L.nthr_A = L.nthr_C = 256;
     L.smem_A = L.smem_C = 0;
     L.fused_reduce = (L.log2Q == 12);
+  } else if (allow_fast && !dbl && P >= 64 && P <= 1024) {
+    // two-stage register column passes (P = 32 P2), one pair per CTA, 256 threads; the
+    // correction runs outside them
+    L.big = true;
+    L.split_corr = true;
+    L.P2 = P / 32;
+    L.G = 1;
+    L.NB = 256 / L.P2;
+    L.ntiles = Q / L.NB;
+    L.nthr_A = L.nthr_C = 256;
+    L.smem_A = L.smem_C = (size_t)big_smem_bytes(L.P2);
   } else {
     L.split_corr = allow_fast && !dbl;
     const int tile = 8192;
@@ -147,7 +162,14 @@ static bool tc_usable(const ConvArgs<float> &a) {
 
 // S_T^T y for every pair into sc.part, then a = scale o (sum of the partials) into sc.acoef
 static fst_status corr_coefficients(Runner *R, ConvArgs<float> &sc, const float *scale) {
-  if (tc_usable(sc)) {
+  const int64_t rows = sc.cplx ? 2 * sc.batch : sc.batch;
+  const int combos = (int)((rows + 3) / 4) * (sc.rpad / 8);
+  if (R->device() && sc.ST && rows <= 32 && sc.rpad <= 64 && combos <= 256 && (uintptr_t)sc.ST % 16 == 0 &&
+      !plain_mode()) {
+    // few signal rows: FP32 CUDA-core partials (the tensor-core tile would be mostly empty)
+    sc.nkb = (int)((sc.N + CORR_BLOCK - 1) / CORR_BLOCK);
+    TRY(R->corr_cc(sc));
+  } else if (tc_usable(sc)) {
     sc.nkb = tc_slices(sc.N);
     TRY(R->corr_tc(sc));
   } else {
@@ -226,11 +248,10 @@ static fst_status run_conv(Runner *R, const Layout &L, ConvArgs<T> a, int64_t np
     // out += S_T a over the whole batch once both lanes have written B y
     R->lanes_join_first();
     R->wait_side();
-    // CUDA-core pass when the batch has enough signal rows to share each staged S_T block
-    // (measured: faster from 64 rows up, slower for 16)
-    const int64_t zrows = sc.cplx ? 2 * sc.batch : sc.batch;
-    const bool zr_ok = sc.rpad <= 64 && zrows >= ZR_ROWS && (!sc.cplx || (uintptr_t)sc.out % 8 == 0);
-    if (zr_ok) TRY(R->z_rmw(sc, (const float *)a.ST));
+    // CUDA-core pass with register-blocked sums (any batch, rpad <= 64), else mma.sync
+    const bool za_ok = sc.ST && sc.rpad <= 64 && (!sc.cplx || (uintptr_t)sc.out % 8 == 0) &&
+                       (uintptr_t)sc.ST % 16 == 0;
+    if (za_ok) TRY(R->zadd(sc));
     else TRY(R->corr_z(sc));
   }
   return FST_OK;
@@ -278,6 +299,7 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
     a.tc_nB = p->tc_nB;
     a.tc_Npad = p->tc_Npad;
     a.twB = p->twB;
+    a.tw8 = p->tw8;
   }
   a.r = full ? (int)p->r : 0;
   a.rpad = (int)p->rpad;
@@ -317,12 +339,13 @@ static fst_status apply_t(fst_plan_t p, const T *y, T *out, int64_t batch, int64
       return run_conv<T>(R, Lc, a, npairs, p->ws);
     }
     fst_status st = run_conv<T>(R, Lc, a, npairs, p->ws);
+    const std::string first_err = st != FST_OK ? std::string(g_err) : std::string();
     void *exec = nullptr;
     long long nodes = 0;
     fst_status st2 = R->graph_end(&exec, &nodes);
     if (st != FST_OK) {
       if (exec) R->graph_destroy(exec);
-      return st;
+      return fail(st, first_err);   // the failure inside the recording, not its consequence
     }
     TRY(st2);
     if (p->graphs.size() >= 8) {
@@ -630,14 +653,34 @@ static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, in
         tb[256 + t * 256 + k] = make_float2((float)cos(ang), (float)sin(ang));
       }
     }
+    for (int t = 0; t < 1024; ++t) {
+      const double ang = -2.0 * M_PI * (double)t / 1024.0;
+      tb[TWB_P_OFF + t] = make_float2((float)cos(ang), (float)sin(ang));
+    }
     if ((s = R->alloc((void **)&p->twB, tb.size() * sizeof(float2))) != FST_OK) return bail(s);
     if ((s = R->h2d(p->twB, tb.data(), tb.size() * sizeof(float2))) != FST_OK) return bail(s);
+    if (R->device()) {
+      // the 8192-point row FFT: W_8192^j (j < 4096), then [t][k] W_32^{kt}, W_512^{kt}, W_8192^{kt}
+      std::vector<float2> t8(TW8_WORDS);
+      auto w = [](double num, double den) {
+        const double ang = -2.0 * M_PI * num / den;
+        return make_float2((float)cos(ang), (float)sin(ang));
+      };
+      for (int j = 0; j < 4096; ++j) t8[TW8_R2 + j] = w(j, 8192.0);
+      for (int t = 0; t < 16; ++t) {
+        for (int k = 0; k < 2; ++k) t8[TW8_32 + t * 2 + k] = w(k * t, 32.0);
+        for (int k = 0; k < 32; ++k) t8[TW8_512 + t * 32 + k] = w(k * t, 512.0);
+        for (int k = 0; k < 512; ++k) t8[TW8_8192 + t * 512 + k] = w(k * t, 8192.0);
+      }
+      if ((s = R->alloc((void **)&p->tw8, t8.size() * sizeof(float2))) != FST_OK) return bail(s);
+      if ((s = R->h2d(p->tw8, t8.data(), t8.size() * sizeof(float2))) != FST_OK) return bail(s);
+    }
   }
 
   Scoped sc(R);
   sc.ptrs.clear();
   const Layout L64 = make_layout(N, p->log2M, true, 0);
-  const Layout L32 = make_layout(N, p->log2M, false, 0);
+  const Layout L32 = make_layout(N, p->log2M, false, 0);   // FP32 P, Q do not depend on the kernels
 
   // sinc spectrum: forward FFT (FP64) of the even embedding c of the first row of B
   double *cvec, *spec_unit;
@@ -821,7 +864,7 @@ void destroy_plan(fst_plan_t p) {
     for (auto &e : p->graphs) R->graph_destroy(e.exec);
     p->graphs.clear();
     void *bufs[] = {p->spec32, p->ST32, p->D32, p->spec64, p->ST64, p->D64, p->ST32_hl, p->STt, p->spec_unit,
-                    p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->twB, p->ws};
+                    p->tw32h, p->tw32l, p->tw64h, p->tw64l, p->twB, p->tw8, p->ws};
     for (void *b : bufs)
       if (b) R->release(b);
     delete R;
@@ -1216,6 +1259,7 @@ static fst_status coeffs_t(fst_plan_t p, const T *y, c2<T> *out, int64_t batch, 
     ca.N = N;
     ca.r = (int)p->r;
     ca.rpad = (int)p->rpad;
+    ca.ST = p->ST32;
     ca.ST_hl = p->ST32_hl;
     ca.pair0 = 0;
     ca.npairs = npairs;
@@ -1595,15 +1639,173 @@ fst_status fst_emu_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, c
 // ===========================================================================
 namespace fst {
 
+// next buffer of the signature's state: allocated (and filled from `init`) on the first call,
+// reused in the same order afterwards (same signature, same sizes and contents)
+static fst_status ragged_buf(Runner *R, RaggedState &st, size_t bytes, const void *init, void **out) {
+  if (st.next < st.bufs.size()) {
+    *out = st.bufs[st.next++];
+    return FST_OK;
+  }
+  void *b = nullptr;
+  TRY(R->alloc(&b, std::max<size_t>(bytes, 16)));
+  st.bufs.push_back(b);
+  st.next = st.bufs.size();
+  if (init) TRY(R->h2d(b, init, bytes));
+  *out = b;
+  return FST_OK;
+}
+
+static bool autotune_enabled() {
+  const char *s = getenv("FST_AUTOTUNE");
+  return !(s && s[0] == '0');
+}
+
+// The four-step signals of a ragged batch (FP32 device plans), by FFT length class M:
+//   1. the correction coefficients a_i = D_i o S_T,i^T y_i of every signal (one launch over
+//      (signal, 2048-sample chunk) items, one reduction launch);
+//   2. per class, launch groups of signals through the batched column / row / column passes
+//      (each signal a pair slot with its own data, length and spectrum), B y only;
+//   3. out_i += S_T,i a_i over all items (one launch).
+// The pairs per launch group of each class are picked on the first call (autotuner: the
+// candidate groupings of 16 .. 256 MiB of intermediate are timed with device events and the
+// fastest kept; the grouping does not change the arithmetic, so results do not depend on it).
+static fst_status ragged_fourstep_f32(const fst_plan_t *plans, const void *const *y, void *const *out,
+                                      const std::vector<int64_t> &idx, bool cplx, RaggedState &st) {
+  Runner *R = plans[idx[0]]->R;
+  const int nsig = (int)idx.size();
+  // correction descriptors and items
+  std::vector<RSig> sig(nsig);
+  std::vector<RItem> items;
+  int64_t poff = 0;
+  for (int i = 0; i < nsig; ++i) {
+    fst_plan_t p = plans[idx[i]];
+    RSig &q = sig[i];
+    q.y = (const float *)y[idx[i]];
+    q.out = (float *)out[idx[i]];
+    q.ST = p->ST32;
+    q.D = p->D32;
+    q.N = p->N;
+    q.r = (int)p->r;
+    q.rpad = (int)p->rpad;
+    q.nK = (int)(((p->N + 1) / 2 + CORR_BLOCK - 1) / CORR_BLOCK);   // chunks of the folded half
+    q.part = poff;
+    for (int w = 0; w < 4; ++w) q.odd[w] = 0;
+    for (int j = 0; j < (int)p->r; ++j)
+      if (p->idx[j] & 1) q.odd[j >> 5] |= 1u << (j & 31);
+    poff += (int64_t)q.nK * 2 * q.rpad;
+    if (p->r > 0)
+      for (int c = 0; c < q.nK; ++c) items.push_back({i, c});
+  }
+  void *dsig, *ditems, *dpart, *dacoef;
+  TRY(ragged_buf(R, st, sig.size() * sizeof(RSig), sig.data(), &dsig));
+  TRY(ragged_buf(R, st, std::max<size_t>(1, items.size()) * sizeof(RItem), items.empty() ? nullptr : items.data(),
+                 &ditems));
+  TRY(ragged_buf(R, st, (size_t)std::max<int64_t>(poff, 1) * sizeof(float), nullptr, &dpart));
+  TRY(ragged_buf(R, st, (size_t)nsig * 2 * RC_RMAX * sizeof(float), nullptr, &dacoef));
+  TRY(R->rcorr((const RSig *)dsig, nsig, (const RItem *)ditems, (int)items.size(), cplx ? 1 : 0, (float *)dpart,
+               (float *)dacoef));
+
+  // length classes
+  std::vector<std::vector<int>> cls(32);
+  for (int i = 0; i < nsig; ++i) cls[plans[idx[i]]->log2M].push_back(i);
+  if (st.chunk.empty()) {
+    st.chunk.assign(32, 0);
+    st.tune_ms.assign(32, 0.0);
+  }
+  // one intermediate workspace for every class (they run one after the other): 256 MiB at most
+  size_t ws_max = 0;
+  for (int lg = 0; lg < 32; ++lg)
+    if (!cls[lg].empty())
+      ws_max = std::max(ws_max, std::min<size_t>((size_t)cls[lg].size(), std::max<size_t>(1, (256u << 20) >> (lg + 3))) *
+                                    ((size_t)8 << lg));
+  void *dws;
+  TRY(ragged_buf(R, st, ws_max, nullptr, &dws));
+  for (int lg = 0; lg < 32; ++lg) {
+    if (cls[lg].empty()) continue;
+    const std::vector<int> &c = cls[lg];
+    const int64_t cnt = (int64_t)c.size();
+    fst_plan_t p0 = plans[idx[c[0]]];
+    int64_t Nmax = 0;
+    std::vector<RPair<float>> rp(cnt);
+    for (int64_t k = 0; k < cnt; ++k) {
+      fst_plan_t p = plans[idx[c[k]]];
+      rp[k].y = (const float *)y[idx[c[k]]];
+      rp[k].out = (float *)out[idx[c[k]]];
+      rp[k].spec = p->spec32;
+      rp[k].N = p->N;
+      Nmax = std::max(Nmax, p->N);
+    }
+    void *drp;
+    TRY(ragged_buf(R, st, rp.size() * sizeof(RPair<float>), rp.data(), &drp));
+    const Layout L = make_layout(Nmax, lg, false, 8, true);
+    ConvArgs<float> a{};
+    a.rp = (const RPair<float> *)drp;
+    a.batch = cnt;
+    a.cplx = cplx ? 1 : 0;
+    a.N = Nmax;
+    a.log2M = L.log2M;
+    a.log2P = L.log2P;
+    a.log2Q = L.log2Q;
+    a.Pnz = L.Pnz;
+    a.NB = L.NB;
+    a.G = L.G;
+    a.r = 0;
+    a.rpad = 8;
+    a.tw = plan_tw<float>(p0);
+    a.twB = p0->twB;
+    a.tw8 = p0->tw8;
+    a.inter = (float2 *)dws;
+    a.mode = MODE_CONV;
+    auto run_groups = [&](int64_t chunk) -> fst_status {
+      for (int64_t q0 = 0; q0 < cnt; q0 += chunk) {
+        a.pair0 = q0;
+        a.npairs = std::min<int64_t>(chunk, cnt - q0);
+        TRY(R->passA(a, L));
+        TRY(R->passB(a, L));
+        TRY(R->passC(a, L));
+      }
+      return FST_OK;
+    };
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(ws_max >> (lg + 3)));
+    if (st.chunk[lg] == 0) {
+      int64_t best = std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)((128u << 20) >> (lg + 3))));
+      double best_ms = 0.0;
+      // in place (y == out) a second run would read its own output: no timing runs then
+      bool inplace = false;
+      for (int64_t k = 0; k < cnt; ++k) inplace = inplace || y[idx[c[k]]] == out[idx[c[k]]];
+      if (autotune_enabled() && !inplace && !R->user_stream_capturing()) {
+        for (int mb = 16; mb <= 256; mb *= 2) {
+          const int64_t ch = std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)(((size_t)mb << 20) >> (lg + 3))));
+          if (mb > 16 && ch == std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)(((size_t)(mb / 2) << 20) >> (lg + 3)))))
+            continue;   // same grouping as the previous candidate
+          TRY(run_groups(ch));   // warm
+          double ms = 0.0;
+          TRY(R->timer(0, nullptr));
+          TRY(run_groups(ch));
+          TRY(R->timer(1, &ms));
+          if (best_ms == 0.0 || ms < best_ms) {
+            best_ms = ms;
+            best = ch;
+          }
+        }
+      }
+      st.chunk[lg] = best;
+      st.tune_ms[lg] = best_ms;
+    }
+    TRY(run_groups(st.chunk[lg]));
+  }
+  return R->rzadd((const RSig *)dsig, (const RItem *)ditems, (int)items.size(), cplx ? 1 : 0, (const float *)dacoef);
+}
+
 template <typename T>
 static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count,
-                           bool cplx, std::vector<void *> &desc_bufs) {
+                           bool cplx, RaggedState &st) {
   const bool dbl = sizeof(T) == 8;
+  st.next = 0;
   // single-CTA signals by FFT length, one launch each
   std::vector<std::vector<RaggedDesc<T>>> buckets(32);
   std::vector<int> maxr(32, 0);
   std::vector<int64_t> others;
-  size_t reuse = 0;
   for (int64_t i = 0; i < count; ++i) {
     fst_plan_t p = plans[i];
     const Layout &L = dbl ? p->lay64 : p->lay32;
@@ -1631,14 +1833,7 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
     Runner *R = p0->R;
     Layout L = make_layout(p0->N, lg, dbl, maxr[lg], false);
     void *dd = nullptr;
-    if (reuse < desc_bufs.size()) {
-      dd = desc_bufs[reuse++];   // same signature as the call that filled it
-    } else {
-      TRY(R->alloc(&dd, buckets[lg].size() * sizeof(RaggedDesc<T>)));
-      desc_bufs.push_back(dd);
-      reuse = desc_bufs.size();
-      TRY(R->h2d(dd, buckets[lg].data(), buckets[lg].size() * sizeof(RaggedDesc<T>)));
-    }
+    TRY(ragged_buf(R, st, buckets[lg].size() * sizeof(RaggedDesc<T>), buckets[lg].data(), &dd));
     ConvArgs<T> base{};
     base.batch = 1;
     base.cplx = cplx ? 1 : 0;
@@ -1649,12 +1844,23 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
     base.npairs = 1;
     TRY(R->small_ragged((const RaggedDesc<T> *)dd, (int)buckets[lg].size(), base, L));
   }
-  for (int64_t i : others) TRY(run_apply(plans[i], y[i], out[i], 1, 0, cplx ? (dbl ? FST_C128 : FST_C64) : (dbl ? FST_F64 : FST_F32), true));
+  if (others.empty()) return FST_OK;
+  // FP32 device plans: batched four-step path; otherwise one call per signal
+  bool batched = !dbl;
+  for (int64_t i : others) {
+    fst_plan_t p = plans[i];
+    batched = batched && p->R->device() && p->lay32.log2Q >= 12 && p->rpad <= RC_RMAX && p->twB && p->ST32 &&
+              (p->lay32.fast || p->lay32.big) && (!cplx || (uintptr_t)out[i] % 8 == 0) &&
+              (!cplx || (uintptr_t)y[i] % 8 == 0);
+  }
+  if (batched) return ragged_fourstep_f32(plans, y, out, others, cplx, st);
+  for (int64_t i : others)
+    TRY(run_apply(plans[i], y[i], out[i], 1, 0, cplx ? (dbl ? FST_C128 : FST_C64) : (dbl ? FST_F64 : FST_F32), true));
   return FST_OK;
 }
 
 fst_status run_ragged(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count, int dtype,
-                      std::vector<void *> &desc_bufs) {
+                      RaggedState &desc_bufs) {
   if (count < 0 || (count > 0 && (!plans || !y || !out))) return fail(FST_EINVAL, "bad arguments");
   for (int64_t i = 0; i < count; ++i)
     if (!plans[i] || !y[i] || !out[i]) return fail(FST_EINVAL, "NULL plan or signal pointer");

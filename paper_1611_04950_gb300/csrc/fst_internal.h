@@ -52,6 +52,12 @@ struct Runner {
   virtual fst_status d2d(void *dst, const void *src, size_t bytes) = 0;
   virtual fst_status zero(void *p, size_t bytes) = 0;
   virtual fst_status sync() = 0;
+  // device timing of the runner's stream: phase 0 records the start, phase 1 the end, waits
+  // for it and writes the elapsed milliseconds
+  virtual fst_status timer(int phase, double *ms) {
+    if (ms) *ms = 0.0;
+    return FST_OK;
+  }
   // FST_ETIMEOUT (and clears it) when a bounded device wait of an earlier launch gave up;
   // with `sync`, first waits for the runner's stream
   virtual fst_status device_status(bool sync) { return sync ? this->sync() : FST_OK; }
@@ -88,6 +94,17 @@ struct Runner {
   virtual fst_status expand(const ExpArgs<double> &a, int64_t nsig) = 0;
   // out += S_T a on CUDA cores (FP32, r <= 64)
   virtual fst_status z_rmw(const ConvArgs<float> &a, const float *ST) { return FST_EUNSUPPORTED; }
+  // ragged four-step signals (FP32 device): correction partials per item, a per signal, and
+  // out += S_T a per item (descriptor arrays in runner memory)
+  virtual fst_status rcorr(const RSig *sigs, int nsig, const RItem *items, int nitems, int cplx, float *part,
+                           float *acoef) { return FST_EUNSUPPORTED; }
+  virtual fst_status rzadd(const RSig *sigs, const RItem *items, int nitems, int cplx, const float *acoef) {
+    return FST_EUNSUPPORTED;
+  }
+  // S_T^T y partials per CORR_BLOCK samples on CUDA cores (FP32, at most 32 signal rows, rpad <= 64)
+  virtual fst_status corr_cc(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
+  // out += S_T a on CUDA cores over the whole batch (FP32, rpad <= 64, any number of rows)
+  virtual fst_status zadd(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
 
   // plan kernels (all pointers in runner memory)
   virtual fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo,
@@ -167,6 +184,7 @@ struct fst_plan_s {
   // stage twiddles of the 4096-point row FFT: [t][k] = W_256^{k t} (k < 16), then
   // W_4096^{k t} (k < 256), t < 16
   float2 *twB = nullptr;
+  float2 *tw8 = nullptr;   // stage twiddles of the 8192-point row FFT (FP64 built)
   double2 *tw64h = nullptr, *tw64l = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -200,10 +218,18 @@ fst_status run_apply_ws(fst_plan_t p, const void *y, void *out, int64_t batch, i
                         void *ws, size_t ws_bytes);
 void destroy_plan(fst_plan_t p);
 bool profiling_enabled();   // per-launch event timing is on (fst_profile_enable)
-// ragged batch on the plans' runners; descriptor buffers it allocates are appended
-// to desc_bufs (the caller owns them); buffers already in desc_bufs are reused
+// Device buffers and launch choices of one ragged signature (owned by the caller): the first
+// call allocates in a fixed order, later calls with the same signature reuse them in that order
+struct RaggedState {
+  std::vector<void *> bufs;
+  size_t next = 0;                  // cursor into bufs during a call
+  bool tuned = false;
+  std::vector<int64_t> chunk;       // pairs per launch group of each four-step length class, by log2 M
+  std::vector<double> tune_ms;      // measured time of the chosen grouping, by log2 M
+};
+// ragged batch on the plans' runners (buffers and tuning in st)
 fst_status run_ragged(const fst_plan_t *plans, const void *const *y, void *const *out, int64_t count, int dtype,
-                      std::vector<void *> &desc_bufs);
+                      RaggedState &st);
 // drop every recorded ragged batch that uses plan p (before p or its workspace is freed)
 void forget_ragged(fst_plan_t p);
 // a test-requested stall of the tcgen05 correction is pending / consume one

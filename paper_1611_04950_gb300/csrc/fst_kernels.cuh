@@ -46,12 +46,21 @@ struct Layout {
   bool fast = false;   // FP32 four-step with P <= 32: register column passes + tensor-core correction
   bool fused_reduce = false;  // the row pass also sums the correction partials (device fast path, Q = 4096)
   bool split_corr = false;    // correction outside the column passes (device FP32 four-step, P > 32)
+  bool big = false;    // FP32 four-step with P = 32 P2, 2 <= P2 <= 32: two-stage register column passes
+  int P2 = 0;
   int log2M = 0, log2P = 0, log2Q = 0;
   int Pnz = 0, NB = 0, G = 1, ntiles = 0;
   int nthr_small = 0, nthr_A = 0, nthr_B = 0, nthr_C = 0;
   size_t smem_small = 0, smem_A = 0, smem_B = 0, smem_C = 0;
   int64_t chunk = 1;   // pairs per launch group
 };
+
+// two-stage column passes (P = 32 P2): columns per CTA, float2 stride between the b-blocks of
+// the shared tile (NB < 16 columns take a 16-word shift, so the two b-blocks a half-warp
+// touches fall in different banks), and the tile's bytes
+__host__ __device__ constexpr int big_nb(int P2) { return 256 / P2; }
+__host__ __device__ constexpr int big_bs(int P2) { return 32 * big_nb(P2) + (big_nb(P2) < 16 ? 8 : 0); }
+__host__ __device__ constexpr int big_smem_bytes(int P2) { return P2 * big_bs(P2) * 8; }
 
 // position of natural frequency index k in the layout's spectrum array
 __host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
@@ -61,6 +70,33 @@ __host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
 }
 
 
+
+// One signal of a ragged four-step batch (its own plan); it takes a whole pair slot (a real
+// signal travels as the real part, the imaginary part is zero)
+template <typename T> struct RPair {
+  const T *y;
+  T *out;
+  const T *spec;   // its spectrum, in the length class's [k1][k2] layout
+  int64_t N;
+};
+
+// Rank-r correction of the four-step signals of a ragged batch (FP32 device): one entry per
+// signal, and work items of CORR_BLOCK samples
+struct RSig {
+  const float *y;      // real: N floats; complex: N (re, im) pairs
+  float *out;
+  const float *ST;     // [N][rpad] FP32; only rows n < ceil(N/2) are read (J-symmetry below)
+  const float *D;      // [r]
+  int64_t N;
+  int r, rpad;
+  int nK;              // ceil(ceil(N/2) / CORR_BLOCK) partial blocks
+  int64_t part;        // offset (floats) of its partials [nK][2][rpad] in the partial buffer
+  uint32_t odd[4];     // bit j: column j is antisymmetric, s(N-1-n) = -s(n) (its index l is odd)
+};
+struct RItem {
+  int sig, chunk;
+};
+constexpr int RC_RMAX = 128;   // coefficient slots per signal and part (rpad <= RC_RMAX)
 
 template <typename T> struct ConvArgs {
   // signals
@@ -94,9 +130,17 @@ template <typename T> struct ConvArgs {
   const float *STt;   // FP32 device plans: S_T^T, K-major, [tc_nB][tc_Npad]
   int tc_nB;
   int64_t tc_Npad;
-  const float2 *twB;  // FP32 device plans: stage twiddles of the 4096-point row FFT
+  const float2 *twB;  // FP32 device plans: stage twiddles of the 4096-point row FFT, then W_1024^t
+  const float2 *tw8;  // FP32 device plans: stage twiddles of the 8192-point row FFT
+  const RPair<T> *rp; // ragged batch: per pair slot signal, length and spectrum (else nullptr)
 };
-constexpr int TWB_WORDS = 16 * 16 + 16 * 256;
+// twB: [t][k] W_256^{k t} (k, t < 16), [t][k] W_4096^{k t} (t < 16, k < 256), W_1024^t (t < 1024)
+constexpr int TWB_P_OFF = 16 * 16 + 16 * 256;
+constexpr int TWB_WORDS = TWB_P_OFF + 1024;
+// tw8 (8192-point rows): W_8192^j (j < 4096), then [t][k] W_32^{k t} (k < 2), W_512^{k t} (k < 32),
+// W_8192^{k t} (k < 512), t < 16
+constexpr int TW8_R2 = 0, TW8_32 = 4096, TW8_512 = TW8_32 + 16 * 2, TW8_8192 = TW8_512 + 16 * 32;
+constexpr int TW8_WORDS = TW8_8192 + 16 * 512;
 
 // TF32 rounding (round to nearest, ties away from zero, 10 mantissa bits kept)
 FST_HD float tf32_round(float x) {
@@ -125,6 +169,12 @@ template <typename T> struct KState {
 // ---- signal access ---------------------------------------------------------
 template <typename T> FST_HD c2<T> load_pair(const ConvArgs<T> &a, int64_t pl, int64_t n) {
   const int64_t p = a.pair0 + pl;
+  if (a.rp) {
+    const RPair<T> &q = a.rp[p];
+    if (n >= q.N) return mk<T>(0, 0);
+    if (a.cplx) return reinterpret_cast<const c2<T> *>(q.y)[n];
+    return mk<T>(q.y[n], (T)0);
+  }
   if (a.cplx) {
     const c2<T> *y2 = reinterpret_cast<const c2<T> *>(a.y);
     return y2[p * a.ld + n];
@@ -136,6 +186,13 @@ template <typename T> FST_HD c2<T> load_pair(const ConvArgs<T> &a, int64_t pl, i
 }
 template <typename T> FST_HD void store_pair(const ConvArgs<T> &a, int64_t pl, int64_t n, c2<T> v) {
   const int64_t p = a.pair0 + pl;
+  if (a.rp) {
+    const RPair<T> &q = a.rp[p];
+    if (n >= q.N) return;
+    if (a.cplx) reinterpret_cast<c2<T> *>(q.out)[n] = v;
+    else q.out[n] = v.x;
+    return;
+  }
   if (a.cplx) {
     reinterpret_cast<c2<T> *>(a.out)[p * a.ld + n] = v;
     return;
@@ -143,6 +200,11 @@ template <typename T> FST_HD void store_pair(const ConvArgs<T> &a, int64_t pl, i
   const int64_t s0 = 2 * p, s1 = 2 * p + 1;
   a.out[s0 * a.ld + n] = v.x;
   if (s1 < a.batch) a.out[s1 * a.ld + n] = v.y;
+}
+
+// spectrum of local pair pl (its own for a ragged batch)
+template <typename T> FST_HD const T *spec_of(const ConvArgs<T> &a, int64_t pl) {
+  return a.rp ? a.rp[a.pair0 + pl].spec : a.spec;
 }
 
 // correction epilogue value: S_T[n,:] . (a_re, a_im)
@@ -338,7 +400,7 @@ FST_HD void passB_body(Ex &ex, const ConvArgs<T> &a, int64_t pl, int k1, c2<T> *
     return;
   }
   ex.phase([&](int tid, St &) {
-    const T *sp = a.spec + (int64_t)k1 * Q;
+    const T *sp = spec_of(a, pl) + (int64_t)k1 * Q;
     for (int i = tid; i < Q; i += nthr) buf[pad(i)] = cscale(buf[pad(i)], ldg(sp + i));
   });
   tile_fft<T, true>(ex, buf, a.log2Q, 1, a.tw);

@@ -35,7 +35,7 @@ EXPORTED = ["fst_plan", "fst_plan_op", "fst_plan_info", "fst_plan_export", "fst_
             "fst_launch_count", "fst_profile_enable", "fst_profile_count", "fst_profile_read",
             "fst_project_noalloc", "fst_noalloc_scratch_bytes", "fst_coeffs", "fst_coeffs_info",
             "fst_adi_shifts", "fst_plan_many", "fst_emu_plan_many", "fst_project_ragged", "fst_expand",
-            "fst_sync", "fst_test_tc_stall"]
+            "fst_sync", "fst_test_tc_stall", "fst_ragged_tuning"]
 
 
 class FSTError(RuntimeError):
@@ -59,6 +59,7 @@ def _load():
         "fst_apply_prolate": ([P, vp, vp, i64, i64, I, vp], I),
         "fst_destroy": ([P], I),
         "fst_sync": ([P, vp], I),
+        "fst_ragged_tuning": ([C.POINTER(P), C.POINTER(vp), C.POINTER(vp), i64, I, C.POINTER(i64), C.POINTER(d)], I),
         "fst_test_tc_stall": ([I, d], I),
         "fst_last_error": ([], C.c_char_p),
         "fst_version": ([], C.c_char_p),
@@ -216,6 +217,19 @@ def fst_project_ragged(handles, y_ptrs, out_ptrs, dtype: int, stream: int = 0):
                                    C.cast(Oa, C.POINTER(C.c_void_p)), n, dtype, C.c_void_p(stream)))
 
 
+def fst_ragged_tuning(handles, y_ptrs, out_ptrs, dtype: int) -> dict:
+    """{log2 M: (signals per launch group, measured ms)} chosen for an earlier ragged call."""
+    n = len(handles)
+    Pa = (C.c_void_p * n)(*handles)
+    Ya = (C.c_void_p * n)(*y_ptrs)
+    Oa = (C.c_void_p * n)(*out_ptrs)
+    pairs = (C.c_int64 * 32)()
+    ms = (C.c_double * 32)()
+    _check(_lib.fst_ragged_tuning(C.cast(Pa, C.POINTER(C.c_void_p)), C.cast(Ya, C.POINTER(C.c_void_p)),
+                                  C.cast(Oa, C.POINTER(C.c_void_p)), n, dtype, pairs, ms))
+    return {lg: (int(pairs[lg]), float(ms[lg])) for lg in range(32) if pairs[lg]}
+
+
 class PlanSet:
     """Plans of a ragged batch (one per signal), built with fst_plan_many."""
 
@@ -238,6 +252,11 @@ class PlanSet:
 
     def info(self, i: int) -> dict:
         return fst_plan_info(self.h[i])
+
+    def tuning(self, ys, outs) -> dict:
+        """The autotuned launch grouping of an earlier project(ys, outs) call."""
+        return fst_ragged_tuning(self.h, [v.data_ptr() for v in ys], [o.data_ptr() for o in outs],
+                                 _dtype_code(ys[0].dtype))
 
     def project(self, ys, outs=None, stream=None):
         """ys: list of (N_i,) device tensors (numpy arrays for an emulated set)."""

@@ -17,6 +17,14 @@ Section 4.1) at the sizes of the benchmark configurations:
   c1m      N=2^20,  W=0.05, eps=1e-6, 64 complex signals, CN(0,1), half of them
            band-limited to |f| <= W (complex64)
   c4m      N=2^22,  W=1/4,  eps=1e-8, 8 N(0,1) + 8 1024-tone signals (FP32)
+
+and the Fourier-extension problem of Section 4.2 (the right-hand side of the normal
+equations B g = F y for a continuous, non-smooth, non-periodic test function; the paper's
+random parameters are not given, so they are drawn here):
+
+  fourier_extension  f(t) = 5 t + sum_{l<500} a_l exp(-|t - mu_l| / sigma_l) on [-1, 1],
+                     a_l ~ N(0, 1/4), mu_l ~ U[-1, 1], sigma_l ~ U[0.02, 0.5] (seed 6),
+                     extension to [-T, T], T = 1.5: N = 2M + 1 coefficients, W = 1/(2T)
 """
 from __future__ import annotations
 
@@ -170,3 +178,48 @@ def gaussian(batch: int, N: int, seed: int, device: str = "cpu", complex_: bool 
         z = (rng.standard_normal((batch, N)) + 1j * rng.standard_normal((batch, N))) / math.sqrt(2)
         return torch.as_tensor(z, device=device)
     return torch.as_tensor(rng.standard_normal((batch, N)), device=device)
+
+
+@dataclass
+class FourierExtension:
+    M: int
+    T: float
+    N: int              # 2M + 1
+    W: float            # 1 / (2T)
+    yhat: np.ndarray    # (F_{N''} f)[m], m = -M..M (complex128): right-hand side of B g = yhat
+    fhat: np.ndarray    # Fourier series coefficients of f on [-1, 1], m = -M..M (complex128)
+    f: object           # callable: f(t) for an array of t in [-1, 1]
+
+
+def fourier_extension(M: int, T: float = 1.5, L: int = 500, seed: int = 6, nquad: int = 1 << 17):
+    """Section 4.2's Fourier-extension set-up with a seeded stand-in for its random test
+    function.  Both coefficient vectors are integrals over [-1, 1] approximated by an
+    FFT of length nquad (the paper likewise uses an FFT):
+      yhat[m] = 1/sqrt(2T) int_{-1}^{1} f(t) exp(-j pi m t / T) dt   (t on a grid of [-T, T))
+      fhat[m] = 1/sqrt(2)  int_{-1}^{1} f(t) exp(-j pi m t) dt       (t on a grid of [-1, 1))
+    for |m| <= M.  (The paper prints + in the exponent of the coefficient formula of
+    Section 4.2 and - in the operator F_{N''} of Section 1.4; - is taken for both.)"""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(L) * 0.5
+    mu = rng.uniform(-1.0, 1.0, L)
+    sig = rng.uniform(0.02, 0.5, L)
+
+    def f(t):
+        t = np.asarray(t, dtype=np.float64)
+        out = 5.0 * t
+        for i in range(0, t.size, 8192):
+            tc = t[i:i + 8192]
+            out[i:i + 8192] += (a[None, :] * np.exp(-np.abs(tc[:, None] - mu[None, :]) / sig[None, :])).sum(1)
+        return out
+
+    m = np.arange(-M, M + 1)
+    tk = -T + 2.0 * T * np.arange(nquad) / nquad
+    fk = np.zeros(nquad)
+    inside = np.abs(tk) <= 1.0
+    fk[inside] = f(tk[inside])
+    Fk = np.fft.fft(fk)
+    yhat = (2.0 * T / nquad) / math.sqrt(2.0 * T) * np.exp(1j * np.pi * m) * Fk[m % nquad]
+    t1 = -1.0 + 2.0 * np.arange(nquad) / nquad
+    F1 = np.fft.fft(f(t1))
+    fhat = (2.0 / nquad) / math.sqrt(2.0) * np.exp(1j * np.pi * m) * F1[m % nquad]
+    return FourierExtension(M=M, T=T, N=2 * M + 1, W=1.0 / (2.0 * T), yhat=yhat, fhat=fhat, f=f)

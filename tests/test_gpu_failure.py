@@ -32,16 +32,17 @@ def _stream():
 
 def test_tc_wait_timeout_is_reported_and_recovered():
     _cuda()
-    N, W = 65536, 1 / 8
+    # 40 signals: batches of more than 32 rows take the tensor-core correction
+    N, W, B = 65536, 1 / 8, 40
     p = F.Plan(N, W, eps=1e-4)
-    y = workloads.gaussian(8, N, seed=41).float().cuda()
+    y = workloads.gaussian(B, N, seed=41).float().cuda()
     ref = p.project(y)
     F.fst_sync(p.h, _stream())
 
     # 1) reported by fst_sync; every output carries the NaN correction
     F.fst_test_tc_stall(1, 0.02)
     out = torch.zeros_like(y)
-    F.fst_project(p.h, y.data_ptr(), out.data_ptr(), 8, N, F.FST_F32, _stream())
+    F.fst_project(p.h, y.data_ptr(), out.data_ptr(), B, N, F.FST_F32, _stream())
     with pytest.raises(F.FSTError) as ei:
         F.fst_sync(p.h, _stream())
     assert ei.value.status == F.FST_ETIMEOUT
@@ -55,11 +56,11 @@ def test_tc_wait_timeout_is_reported_and_recovered():
 
     # 3) reported by the next call on the plan, which enqueues nothing
     F.fst_test_tc_stall(1, 0.02)
-    F.fst_project(p.h, y.data_ptr(), out.data_ptr(), 8, N, F.FST_F32, _stream())
+    F.fst_project(p.h, y.data_ptr(), out.data_ptr(), B, N, F.FST_F32, _stream())
     torch.cuda.synchronize()
     marker = torch.full_like(y, 7.0)
     with pytest.raises(F.FSTError) as ei:
-        F.fst_project(p.h, y.data_ptr(), marker.data_ptr(), 8, N, F.FST_F32, _stream())
+        F.fst_project(p.h, y.data_ptr(), marker.data_ptr(), B, N, F.FST_F32, _stream())
     assert ei.value.status == F.FST_ETIMEOUT
     torch.cuda.synchronize()
     assert torch.all(marker == 7.0)
@@ -69,7 +70,7 @@ def test_tc_wait_timeout_is_reported_and_recovered():
     yh = y.cpu().pin_memory()
     oh = torch.empty_like(yh).pin_memory()
     with pytest.raises(F.FSTError) as ei:
-        F.fst_project_host(p.h, yh.data_ptr(), oh.data_ptr(), 8, F.FST_F32, _stream())
+        F.fst_project_host(p.h, yh.data_ptr(), oh.data_ptr(), B, F.FST_F32, _stream())
     assert ei.value.status == F.FST_ETIMEOUT
     F.fst_sync(p.h, _stream())
     assert torch.equal(p.project_host(yh), ref.cpu())
@@ -135,3 +136,4 @@ def test_ragged_recording_follows_a_moved_workspace():
         ps.project(ys, outs)
     torch.cuda.synchronize()
     _check_ragged(params, ys64, outs)
+

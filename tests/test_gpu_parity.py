@@ -136,6 +136,23 @@ def test_ragged_lengths_fp32_fp64(N, W, eps):
     assert np.all(rel_err(out32, fast, y.numpy()) < 1e-5)
 
 
+@pytest.mark.parametrize("N,W,eps,cplx", [(150001, 0.1, 1e-6, False),     # M = 2^19: P = 128 (P2 = 4)
+                                           (300000, 0.02, 1e-4, True),      # M = 2^20: P = 256 (P2 = 8)
+                                           (1048577, 0.01, 1e-3, False)])   # M = 2^22: P = 1024 (P2 = 32)
+def test_two_stage_column_passes(N, W, eps, cplx):
+    # the FP32 four-step path with P = 32 P2 column rows (two register stages), odd batches,
+    # every row against the FP64 oracle
+    dev = _cuda()
+    p = F.Plan(N, W, eps=eps)
+    o = oplan(N, W, p.K, eps)
+    assert p.r == o.r
+    y = workloads.gaussian(3, N, seed=N % 1000, complex_=cplx)
+    fast = O.fast_project(o, y.numpy().T).T
+    out = p.project(y.to(torch.complex64 if cplx else torch.float32).to(dev)).cpu().numpy()
+    e = rel_err(out, fast, y.numpy())
+    assert np.all(e < 1e-5), e
+
+
 def test_complex_signals():
     dev = _cuda()
     N, W, eps = 20000, 0.05, 1e-6
@@ -215,6 +232,46 @@ def test_other_operators_four_step(op, alpha, cplx):
         # without the 1/(1 + alpha) scaling the result would be off by ~alpha ||B y||
         plain = O.fast_apply(oplan(N, W, p.K, eps), y.numpy().T).T
         assert np.all(rel_err(out, plain, y.numpy()) > 1e-4)
+
+
+def _threshold_K(N, W, lam_min=1e-4):
+    # eigenvalues above lam_min (Section 4.2's truncation): Rayleigh quotients of a window of
+    # the oracle's Slepian vectors beyond round(2NW)
+    K0 = O.default_K(N, W)
+    lo, hi = max(0, K0 - 8), min(N - 1, K0 + 120)
+    lam = O.rayleigh_eigenvalues(O.dpss_window(N, W, lo, hi), W)
+    assert lam[0] > lam_min > lam[-1]
+    return lo + int(np.sum(lam > lam_min))
+
+
+@pytest.mark.parametrize("M", [448, 4096])
+def test_fourier_extension_pinv(M):
+    # Section 4.2: the normal equations B g = F y of the Fourier extension (T = 1.5), solved with
+    # the fast truncated pseudoinverse (eigenvalues below 1e-4 truncated, eps = 1e-5) on the GPU,
+    # FP64 and FP32, against the oracle; for M = 448 also the paper's claim that the extension's
+    # RMS error is at least 10 times below the truncated Fourier series'
+    from tests.test_oracle_fext import rel_rms, synth
+    dev = _cuda()
+    fe = workloads.fourier_extension(M)
+    K = _threshold_K(fe.N, fe.W)
+    p = F.Plan(fe.N, fe.W, K=K, eps=1e-5, op="pinv")
+    o = oplan(fe.N, fe.W, K, 1e-5, "pinv")
+    assert p.r == o.r
+    ref = O.fast_apply(o, fe.yhat)
+    gain = max(1.0, np.abs(o.D).max())
+    nrm = np.linalg.norm(fe.yhat)
+    g64 = p.project(torch.from_numpy(fe.yhat[None, :]).to(dev)).cpu().numpy()[0]
+    g32 = p.project(torch.from_numpy(fe.yhat[None, :].astype(np.complex64)).to(dev)).cpu().numpy()[0]
+    assert np.linalg.norm(g64 - ref) <= 1e-12 * gain * nrm
+    assert np.linalg.norm(g32 - ref) <= 1e-5 * gain * nrm
+    if M <= 1024:
+        t = np.linspace(-1.0, 1.0, 4097)
+        ft = fe.f(t)
+        e_ref = rel_rms(synth(ref, t, fe.T), ft, t)
+        e32 = rel_rms(synth(g32.astype(np.complex128), t, fe.T), ft, t)
+        e_ser = rel_rms(synth(fe.fhat, t, 1.0), ft, t)
+        assert abs(e32 - e_ref) <= 0.02 * e_ref
+        assert e32 * 10 <= e_ser
 
 
 def test_degenerate_K_and_batch_zero():
@@ -427,3 +484,53 @@ def test_ragged_batch_against_oracle_and_replay():
         ref = O.fast_project(op, ys64[i])
         err = np.linalg.norm(outs[i].double().cpu().numpy() - ref) / np.linalg.norm(ys64[i])
         assert err < 1e-5, (i, N, err)
+
+
+def test_ragged_4096_every_signal():
+    # the ragged workload at full size (4096 signals, N log-uniform in [1000, 262144], own W and
+    # eps each): every signal of the batched call against the one-signal-per-call path, a
+    # stratified sample of 48 against the FP64 oracle (spawn pool), and repeated calls (direct
+    # with tuning, recorded, replayed) bit for bit
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from tests._oracle_pool import oracle_fast
+    _cuda()
+    params = workloads.ragged_params(4096, seed=3)
+    ps = F.PlanSet(params)
+    lens = [N for (N, W, e) in params]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    yall = torch.randn(int(offs[-1]), device="cuda", generator=gen)
+    oall = torch.empty_like(yall)
+    ys = [yall[offs[i]:offs[i + 1]] for i in range(len(params))]
+    outs = [oall[offs[i]:offs[i + 1]] for i in range(len(params))]
+    ps.project(ys, outs)
+    first = oall.clone()
+    ps.project(ys, outs)
+    ps.project(ys, outs)
+    torch.cuda.synchronize()
+    assert torch.equal(first, oall)
+    # one fst_project call per signal (the plans' own paths)
+    single = torch.empty_like(yall)
+    stream = torch.cuda.current_stream().cuda_stream
+    for i, h in enumerate(ps.h):
+        F.fst_project(h, ys[i].data_ptr(), single[offs[i]:offs[i + 1]].data_ptr(), 1, 0, F.FST_F32, stream)
+    torch.cuda.synchronize()
+    d = (oall - single).double()
+    num = torch.zeros(len(params), dtype=torch.float64, device="cuda")
+    den = torch.zeros_like(num)
+    seg = torch.repeat_interleave(torch.arange(len(params), device="cuda"),
+                                  torch.as_tensor(lens, device="cuda"))
+    num.index_add_(0, seg, d * d)
+    den.index_add_(0, seg, yall.double() ** 2)
+    rel = torch.sqrt(num / den).cpu().numpy()
+    assert np.all(rel < 2e-6), (int(np.argmax(rel)), float(rel.max()))
+    # stratified sample against the oracle (48 signals spread over the sorted lengths)
+    order = np.argsort(lens)
+    pick = [int(order[k]) for k in np.linspace(0, len(order) - 1, 48).round().astype(int)]
+    jobs = [(params[i][0], params[i][1], params[i][2], ys[i].double().cpu().numpy()) for i in pick]
+    with cf.ProcessPoolExecutor(max_workers=min(16, mp.cpu_count()), mp_context=mp.get_context("spawn")) as ex:
+        refs = list(ex.map(oracle_fast, jobs))
+    for i, ref, job in zip(pick, refs, jobs):
+        err = np.linalg.norm(outs[i].double().cpu().numpy() - ref) / np.linalg.norm(job[3])
+        assert err < 1e-5, (i, params[i], err)
