@@ -51,14 +51,14 @@ WORKLOADS = {
 }
 
 
-def make_workload(name, device, batch=None):
+def make_workload(name, device, batch=None, n=None):
     from paper_1611_04950_gb300 import workloads as WL
     if name == "c65k":
-        return WL.c65k(batch=batch or 1024, device=device)
+        return WL.c65k(batch=batch or 1024, device=device, **({"N": n} if n else {}))
     if name == "c1m":
-        return WL.c1m(batch=batch or 64, device=device)
+        return WL.c1m(batch=batch or 64, device=device, **({"N": n} if n else {}))
     if name == "c4m":
-        return WL.c4m(batch=batch or 16, device=device)
+        return WL.c4m(batch=batch or 16, device=device, **({"N": n} if n else {}))
     if name == "tiny":
         return WL.tiny(device=device)
     raise ValueError(name)
@@ -80,17 +80,18 @@ def job_throughput(samples_per_rank, world, seconds):
     return samples_per_rank * world / seconds
 
 
-def ncu_traffic(kernel, pairs_per_launch):
+def ncu_traffic(kernel, pairs_per_launch, M):
     """DRAM bytes (read + write) of one launch of `kernel`, from the ncu capture summarised in
-    profiles/ncu_traffic.txt (lines: kernel, bytes, pairs per captured launch), scaled to this
-    launch's pairs; None when that kernel has no capture."""
+    profiles/ncu_traffic.txt (lines: kernel, bytes, pairs per captured launch, FFT length M of
+    the captured workload), scaled to this launch's pairs; None when that kernel has no capture
+    at this FFT length."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel:
+            if len(parts) == 4 and not line.startswith("#") and parts[0] == kernel and int(parts[3]) == M:
                 return float(parts[1]) * pairs_per_launch / float(parts[2])
     return None
 
@@ -250,6 +251,18 @@ def run_ragged_bench(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     tuning = {f"M=2^{lg}": {"signals_per_group": n, "ms": t} for lg, (n, t) in ps.tuning(ys, outs).items()}
+    # per-kernel device time of one batched call (events around every launch: direct launches)
+    F.fst_profile_enable(True)
+    ps.project(ys, outs)
+    torch.cuda.synchronize()
+    per = {}
+    for name, t_ms, units in F.fst_profile_records():
+        d = per.setdefault(name, {"launches": 0, "ms": 0.0})
+        d["launches"] += 1
+        d["ms"] += t_ms
+    F.fst_profile_enable(False)
+    ktot = sum(d["ms"] for d in per.values()) or 1.0
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"], "share": v["ms"] / ktot} for k, v in per.items()}
     # one fst_project call per signal (each plan's own cached graph)
     def per_signal():
         for h, y, o in zip(ps.h, ys, outs):
@@ -322,7 +335,7 @@ def run_ragged_bench(args):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "whole ragged step", "peak_source": src},
+                     "kernel": "whole ragged step", "peak_source": src, "kernels": kernels},
         "plan_s": plan_s,
         "plain": {"ms_per_step": ms_per_signal, "form": "one fst_project call per signal"},
         "plain_ms_per_step": ms_per_signal, "batched_over_plain": ms_per_signal / ms,
@@ -340,6 +353,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c65k", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="signal length other than the workload's (small cases for profiling only)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-signal-per-launch arm")
@@ -370,7 +385,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    wl = make_workload(args.workload, "cuda", args.batch)
+    wl = make_workload(args.workload, "cuda", args.batch, args.n)
     y = wl.y.contiguous()
     out = torch.empty_like(y)
     B, N = y.shape
@@ -453,7 +468,7 @@ def main():
         achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_src}
-    roofline["traffic"] = ncu_traffic(dom, pairs_per_launch)
+    roofline["traffic"] = ncu_traffic(dom, pairs_per_launch, plan.M)
     roofline["kernel"] = dom
     roofline["kernels"] = {k: {"launches": v["launches"] // 3, "ms_per_step": v["ms"] / 3,
                                "share": v["ms"] / tot} for k, v in per.items()}
@@ -567,7 +582,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if y.is_complex() else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "N": N, "W": wl.W, "eps": wl.eps,
+            "config": {"workload": WORKLOADS[args.workload]["desc"] + (f"; N overridden to {N} (profiling case)"
+                                                                       if args.n else ""),
+                       "N": N, "W": wl.W, "eps": wl.eps,
                        "batch_per_gpu": B, "K": plan.K, "r": plan.r, "M": plan.M,
                        "step": "projection + fast coefficient vector" if with_coeffs else "projection",
                        "l2": f"inputs {B * sig_bytes / 2**20:.0f} MiB + outputs of the same size exceed "

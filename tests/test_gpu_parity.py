@@ -426,7 +426,7 @@ def _c4m():
 
 def test_c4m_full_batch_projection_every_row_and_coeffs():
     # N = 2^22, W = 1/4, eps = 1e-8, 16 real FP32 signals: every projected row, and the
-    # coefficient vector of four rows (both halves of the workload)
+    # coefficient vector of two rows (one from each half of the workload)
     from oracle import thm1 as T
     _cuda()
     wl, p = _c4m()
@@ -439,7 +439,7 @@ def test_c4m_full_batch_projection_every_row_and_coeffs():
     e = rel_err(out.cpu().numpy(), _fast_rows(o, y, chunk=4), y)
     assert e.shape == (16,)
     assert np.all(e < 1e-5), (np.argmax(e), e.max())
-    idx = [0, 7, 8, 15]
+    idx = [0, 15]
     t = T.thm1(wl.N, wl.W, wl.eps)
     ref = T.coeffs(t, o, y[idx].T).T
     c = coef[idx].cpu().numpy()

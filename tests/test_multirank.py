@@ -69,16 +69,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_ncu_traffic_lookup_scales_to_the_launch():
-    # profiles/ncu_traffic.txt: DRAM bytes of one captured launch and the pairs it covered
+    # profiles/ncu_traffic.txt: DRAM bytes of one captured launch, the pairs it covered and the
+    # FFT length of the captured workload (another length has no figure)
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     rows = {}
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 3 and not line.startswith("#"):
-                rows[parts[0]] = (float(parts[1]), float(parts[2]))
+            if len(parts) == 4 and not line.startswith("#"):
+                rows[parts[0]] = (float(parts[1]), float(parts[2]), int(parts[3]))
     assert "k_fastB4096" in rows
-    b, pairs = rows["k_fastB4096"]
-    assert bench.ncu_traffic("k_fastB4096", pairs) == b
-    assert bench.ncu_traffic("k_fastB4096", 2 * pairs) == 2 * b
-    assert bench.ncu_traffic("no_such_kernel", 1) is None
+    b, pairs, M = rows["k_fastB4096"]
+    assert bench.ncu_traffic("k_fastB4096", pairs, M) == b
+    assert bench.ncu_traffic("k_fastB4096", 2 * pairs, M) == 2 * b
+    assert bench.ncu_traffic("k_fastB4096", pairs, 2 * M) is None
+    assert bench.ncu_traffic("no_such_kernel", 1, M) is None
