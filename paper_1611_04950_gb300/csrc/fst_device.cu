@@ -224,6 +224,157 @@ template <typename T> __global__ void __launch_bounds__(COEF_THREADS) k_coef_low
   DevExS<CState<T>> ex;
   coef_lowrank_body<T>(ex, a, (int64_t)blockIdx.y, (int)blockIdx.x, reinterpret_cast<T *>(smem));
 }
+// The raw low-rank sums of coef_lowrank_body for real FP32 signals, CL_SG signals per block:
+// the generated columns (CF-ADI Z and J Z, centred monomials) and the phase ramps do not depend
+// on the signal, so each value is formed once per sample and weighted by every signal of the
+// group (for real y, v = ph y: sum col ph y = sum (col ph) y).  Same partial layout as
+// coef_lowrank_body (the conjugate variants are copied at the end).  A round reduces 32 values
+// (two columns' f and r sums, or four monomials, for the group's signals; re and im) over the
+// block in a fixed order: [value][thread] in shared memory, 8 parts of 32 threads, then the
+// parts.  grid (nchunks, ceil(batch / CL_SG)), COEF_THREADS threads.
+constexpr int CL_SG = 4, CL_VALS = 32, CL_PARTS = COEF_THREADS / CL_VALS;
+constexpr int CL_LD = COEF_THREADS + 16;
+__global__ void __launch_bounds__(COEF_THREADS, 2) k_coef_lowrank_r4(const CoefArgs<float> a) {
+  __shared__ float red[CL_VALS * CL_LD + CL_VALS * CL_PARTS];
+  const int tid = threadIdx.x;
+  const int chunk = blockIdx.x;
+  const int64_t s0 = (int64_t)blockIdx.y * CL_SG;
+  const int ns = (int)((a.batch - s0 < CL_SG) ? a.batch - s0 : CL_SG);
+  const int64_t n0 = (int64_t)chunk * COEF_CHUNK;
+  const float half = 0.5f, Nd = (float)a.N, cen = (float)(0.5 * (double)(a.N - 1)), invN = (float)(1.0 / (double)a.N);
+  float y[COEF_E][CL_SG];
+  bool in[COEF_E];
+#pragma unroll
+  for (int e = 0; e < COEF_E; ++e) {
+    const int64_t n = n0 + tid + (int64_t)e * COEF_THREADS;
+    in[e] = n < a.N;
+#pragma unroll
+    for (int s = 0; s < CL_SG; ++s) y[e][s] = (in[e] && s < ns) ? a.y[(s0 + s) * a.ld + n] : 0.f;
+  }
+  // fixed-order block sum of acc[0 .. CL_VALS) -> red's tail (value v at red[CL_VALS*CL_LD + v])
+  auto reduce = [&](const float *acc) {
+#pragma unroll
+    for (int v = 0; v < CL_VALS; ++v) red[v * CL_LD + tid] = acc[v];
+    __syncthreads();
+    {
+      const int v = tid / CL_PARTS, p = tid % CL_PARTS;
+      float sum = 0.f;
+#pragma unroll 8
+      for (int i = 0; i < COEF_THREADS / CL_PARTS; ++i) sum += red[v * CL_LD + p + CL_PARTS * i];
+      __syncthreads();
+      red[CL_VALS * CL_LD + v * CL_PARTS + p] = sum;
+    }
+    __syncthreads();
+    if (tid < CL_VALS) {
+      float sum = 0.f;
+#pragma unroll
+      for (int p = 0; p < CL_PARTS; ++p) sum += red[CL_VALS * CL_LD + tid * CL_PARTS + p];
+      red[tid] = sum;   // the first values of the (now free) thread area
+    }
+    __syncthreads();
+  };
+  auto out_of = [&](int s) { return a.part + (((s0 + s) * a.nchunks + chunk) * (int64_t)a.nraw) * 2; };
+  const int vbase[4] = {0, 2 * a.rH + a.DA, 4 * a.rH + 2 * a.DA, 4 * a.rH + 2 * a.DA + a.DB};
+  for (int variant = 0; variant < 4; variant += 2) {   // real y: the conjugate variants are copies
+    const bool useA = variant == 0;
+    float2 ph[COEF_E];
+#pragma unroll
+    for (int e = 0; e < COEF_E; ++e) {
+      const int64_t n = n0 + tid + (int64_t)e * COEF_THREADS;
+      ph[e] = in[e] ? (useA ? a.phA[n] : a.phB[n]) : make_float2(0.f, 0.f);
+    }
+    int obase = vbase[variant];
+    if (useA) {
+      float zf[COEF_E], zr[COEF_E];
+#pragma unroll
+      for (int e = 0; e < COEF_E; ++e) {
+        const float x = (float)(n0 + tid + (int64_t)e * COEF_THREADS) + half, xr = Nd - x;
+        zf[e] = in[e] ? coef_div(a.zfirst[0], x + a.zshift[0]) : 0.f;
+        zr[e] = in[e] ? coef_div(a.zfirst[0], xr + a.zshift[0]) : 0.f;
+      }
+      for (int k0 = 0; k0 < a.rH; k0 += 2) {
+        const int kc = (a.rH - k0 < 2) ? a.rH - k0 : 2;
+        float acc[CL_VALS];   // [column kk][f / r][signal][re / im]
+#pragma unroll
+        for (int v = 0; v < CL_VALS; ++v) acc[v] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          if (kk >= kc) break;
+          const int k = k0 + kk;
+          const float pk = a.zshift[k], pk1 = k > 0 ? a.zshift[k - 1] : 0.f, sc = a.zfirst[k];
+#pragma unroll
+          for (int e = 0; e < COEF_E; ++e) {
+            const float x = (float)(n0 + tid + (int64_t)e * COEF_THREADS) + half, xr = Nd - x;
+            if (k > 0 && in[e]) {
+              zf[e] = coef_div(sc * (x - pk1) * zf[e], x + pk);
+              zr[e] = coef_div(sc * (xr - pk1) * zr[e], xr + pk);
+            }
+            const float cfx = zf[e] * ph[e].x, cfy = zf[e] * ph[e].y;
+            const float crx = zr[e] * ph[e].x, cry = zr[e] * ph[e].y;
+#pragma unroll
+            for (int s = 0; s < CL_SG; ++s) {
+              acc[kk * 16 + 0 * 8 + 2 * s] = fmaf(cfx, y[e][s], acc[kk * 16 + 0 * 8 + 2 * s]);
+              acc[kk * 16 + 0 * 8 + 2 * s + 1] = fmaf(cfy, y[e][s], acc[kk * 16 + 0 * 8 + 2 * s + 1]);
+              acc[kk * 16 + 1 * 8 + 2 * s] = fmaf(crx, y[e][s], acc[kk * 16 + 1 * 8 + 2 * s]);
+              acc[kk * 16 + 1 * 8 + 2 * s + 1] = fmaf(cry, y[e][s], acc[kk * 16 + 1 * 8 + 2 * s + 1]);
+            }
+          }
+        }
+        reduce(acc);
+        if (tid < 16 * kc) {
+          const int kk = tid / 16, fr = (tid / 8) & 1, s = (tid / 2) & 3, c = tid & 1;
+          if (s < ns) out_of(s)[2 * (obase + fr * a.rH + k0 + kk) + c] = red[tid];
+        }
+        __syncthreads();
+      }
+      obase += 2 * a.rH;
+    }
+    // centred monomials u^i, four per round
+    const int D = useA ? a.DA : a.DB;
+    float up[COEF_E];
+#pragma unroll
+    for (int e = 0; e < COEF_E; ++e) up[e] = 1.f;
+    for (int i0 = 0; i0 < D; i0 += 4) {
+      const int ic = (D - i0 < 4) ? D - i0 : 4;
+      float acc[CL_VALS];   // [monomial ii][signal][re / im]
+#pragma unroll
+      for (int v = 0; v < CL_VALS; ++v) acc[v] = 0.f;
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) {
+        if (ii >= ic) break;
+#pragma unroll
+        for (int e = 0; e < COEF_E; ++e) {
+          const float u = ((float)(n0 + tid + (int64_t)e * COEF_THREADS) - cen) * invN;
+          if (i0 + ii > 0) up[e] *= u;
+          const float cx = up[e] * ph[e].x, cy = up[e] * ph[e].y;
+#pragma unroll
+          for (int s = 0; s < CL_SG; ++s) {
+            acc[ii * 8 + 2 * s] = fmaf(cx, y[e][s], acc[ii * 8 + 2 * s]);
+            acc[ii * 8 + 2 * s + 1] = fmaf(cy, y[e][s], acc[ii * 8 + 2 * s + 1]);
+          }
+        }
+      }
+      reduce(acc);
+      if (tid < 8 * ic) {
+        const int ii = tid / 8, s = (tid / 2) & 3, c = tid & 1;
+        if (s < ns) out_of(s)[2 * (obase + i0 + ii) + c] = red[tid];
+      }
+      __syncthreads();
+    }
+  }
+  // conjugate variants (D_A y, D_B y) of real input
+  const int n0c = 2 * a.rH + a.DA, n2c = a.DB;
+  for (int s = 0; s < ns; ++s) {
+    float *out = out_of(s);
+    for (int i = tid; i < n0c + n2c; i += COEF_THREADS) {
+      const int src = (i < n0c) ? vbase[0] + i : vbase[2] + (i - n0c);
+      const int dst = (i < n0c) ? vbase[1] + i : vbase[3] + (i - n0c);
+      out[2 * dst] = out[2 * src];
+      out[2 * dst + 1] = -out[2 * src + 1];
+    }
+  }
+}
+
 template <typename T> __global__ void __launch_bounds__(COEF_THREADS) k_coef_st(const CoefArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   DevExS<CState<T>> ex;
@@ -884,6 +1035,14 @@ struct DevRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status coef_lowrank_t(const CoefArgs<T> &a) {
+    if (sizeof(T) == 4 && !a.cplx && a.batch >= 2) {
+      // real FP32 batches: four signals share every generated column
+      const CoefArgs<float> &af = *reinterpret_cast<const CoefArgs<float> *>(&a);
+      dim3 grid((unsigned)af.nchunks, (unsigned)((af.batch + CL_SG - 1) / CL_SG));
+      PROF("k_coef_lowrank_r4", 0, (k_coef_lowrank_r4<<<grid, COEF_THREADS, 0, cur>>>(af)));
+      LAUNCHED("k_coef_lowrank_r4");
+      return FST_OK;
+    }
     const size_t smem = (size_t)COEF_RED_WORDS * sizeof(T);
     dim3 grid((unsigned)a.nchunks, (unsigned)a.batch);
     PROF("k_coef_lowrank", 0, (k_coef_lowrank<T><<<grid, COEF_THREADS, smem, cur>>>(a)));

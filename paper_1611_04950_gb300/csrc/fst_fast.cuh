@@ -1068,57 +1068,78 @@ __global__ void __launch_bounds__(CC_THREADS) k_corr_cc(const ConvArgs<float> a)
 //   k_rzadd        item: out(n) and out(N-1-n) += ... for the chunk's n (thread per n)
 // acoef: [signal][2][RC_RMAX]
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool rs_odd(const RSig &q, int j) { return (q.odd[j >> 5] >> (j & 31)) & 1u; }
+// one folded sample of k_rcorr_part: the thread's float4 of S_T row n against y(n) +- y(N-1-n),
+// the sign by the parity bits `odd` of its four columns
+__device__ __forceinline__ void rcorr_one(const RSig &q, int cplx, const float4 *S4, int tpr, int jq, unsigned odd,
+                                          int64_t n, float *ar, float *ai) {
+  const int64_t m = q.N - 1 - n;
+  float yr, yi = 0.f, mr = 0.f, mi = 0.f;
+  if (cplx) {
+    const float2 v = reinterpret_cast<const float2 *>(q.y)[n];
+    yr = v.x;
+    yi = v.y;
+    if (m != n) {
+      const float2 w = reinterpret_cast<const float2 *>(q.y)[m];
+      mr = w.x;
+      mi = w.y;
+    }
+  } else {
+    yr = q.y[n];
+    if (m != n) mr = q.y[m];
+  }
+  const float4 s4 = __ldg(S4 + n * tpr + jq);
+  const float pr = yr + mr, dr = yr - mr, pi = yi + mi, di = yi - mi;
+  ar[0] = fmaf(s4.x, (odd & 1u) ? dr : pr, ar[0]);
+  ar[1] = fmaf(s4.y, (odd & 2u) ? dr : pr, ar[1]);
+  ar[2] = fmaf(s4.z, (odd & 4u) ? dr : pr, ar[2]);
+  ar[3] = fmaf(s4.w, (odd & 8u) ? dr : pr, ar[3]);
+  ai[0] = fmaf(s4.x, (odd & 1u) ? di : pi, ai[0]);
+  ai[1] = fmaf(s4.y, (odd & 2u) ? di : pi, ai[1]);
+  ai[2] = fmaf(s4.z, (odd & 4u) ? di : pi, ai[2]);
+  ai[3] = fmaf(s4.w, (odd & 8u) ? di : pi, ai[3]);
+}
 
+// The chunk's S_T rows are one contiguous block ([n][rpad]); the block streams it in 16-byte
+// pieces: thread t takes the float4 jq = t mod tpr (tpr = rpad/4 threads per row) of rows
+// t / tpr, t / tpr + rpr, ... (rpr = 256 / tpr rows per round, four rounds in flight), folding
+// y(n) +- y(N-1-n) by the parity of each of its four columns.  Fixed-order sums at the end.
 __global__ void __launch_bounds__(256) k_rcorr_part(const RSig *sigs, const RItem *items, int cplx, float *part) {
-  __shared__ float red[8][4][32];
+  __shared__ float red[2048];   // [row slot][comp][j]: rpr * 2 * rpad <= 2048 floats
   const RItem it = items[blockIdx.x];
   const RSig q = sigs[it.sig];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tpr = q.rpad / 4, rpr = 256 / tpr;
+  const int slot = threadIdx.x / tpr, jq = threadIdx.x % tpr;
+  const bool active = slot < rpr;
   const int64_t H = (q.N + 1) / 2;
   const int64_t n0 = (int64_t)it.chunk * CORR_BLOCK;
   const int64_t nend = (H - n0 < CORR_BLOCK) ? H : n0 + CORR_BLOCK;
-  for (int j0 = 0; j0 < q.rpad; j0 += 64) {
-    const int ja = j0 + lane, jb = j0 + 32 + lane;
-    const bool oa = rs_odd(q, ja & (RC_RMAX - 1)), ob = rs_odd(q, jb & (RC_RMAX - 1));
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t n = n0 + w; n < nend; n += 8) {
-      const int64_t m = q.N - 1 - n;
-      float yr, yi = 0.f, mr = 0.f, mi = 0.f;
-      if (cplx) {
-        const float2 v = reinterpret_cast<const float2 *>(q.y)[n];
-        yr = v.x;
-        yi = v.y;
-        if (m != n) {
-          const float2 u = reinterpret_cast<const float2 *>(q.y)[m];
-          mr = u.x;
-          mi = u.y;
-        }
-      } else {
-        yr = q.y[n];
-        if (m != n) mr = q.y[m];
-      }
-      const float *row = q.ST + n * q.rpad;
-      const float sa = ja < q.rpad ? __ldg(row + ja) : 0.f;
-      const float sb = jb < q.rpad ? __ldg(row + jb) : 0.f;
-      acc[0] = fmaf(sa, oa ? yr - mr : yr + mr, acc[0]);
-      acc[1] = fmaf(sa, oa ? yi - mi : yi + mi, acc[1]);
-      acc[2] = fmaf(sb, ob ? yr - mr : yr + mr, acc[2]);
-      acc[3] = fmaf(sb, ob ? yi - mi : yi + mi, acc[3]);
+  const int jb = (4 * jq) & (RC_RMAX - 1);
+  // 4 j never straddle a word (jb % 4 == 0); the word is read from the descriptor in global
+  // memory (a runtime index into the register copy would put it in local memory)
+  const unsigned odd = (__ldg(&sigs[it.sig].odd[jb >> 5]) >> (jb & 31)) & 15u;
+  float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+  if (active) {
+    const float4 *S4 = reinterpret_cast<const float4 *>(q.ST);
+    int64_t n = n0 + slot;
+    for (; n + 3 * rpr < nend; n += 4 * rpr) {
+      rcorr_one(q, cplx, S4, tpr, jq, odd, n, ar, ai);
+      rcorr_one(q, cplx, S4, tpr, jq, odd, n + rpr, ar, ai);
+      rcorr_one(q, cplx, S4, tpr, jq, odd, n + 2 * rpr, ar, ai);
+      rcorr_one(q, cplx, S4, tpr, jq, odd, n + 3 * rpr, ar, ai);
     }
+    for (; n < nend; n += rpr) rcorr_one(q, cplx, S4, tpr, jq, odd, n, ar, ai);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) red[w][u][lane] = acc[u];
-    __syncthreads();
-    if (threadIdx.x < 128) {
-      const int comp = threadIdx.x >> 6, jj = threadIdx.x & 63;   // jj < 32: ja; else jb
-      const int u = (jj < 32 ? 0 : 2) + comp, l = jj & 31;
-      float sum = 0.f;
-#pragma unroll
-      for (int ww = 0; ww < 8; ++ww) sum += red[ww][u][l];
-      const int j = j0 + jj;
-      if (j < q.rpad) part[q.part + ((int64_t)it.chunk * 2 + comp) * q.rpad + j] = sum;
+    for (int u = 0; u < 4; ++u) {
+      red[(slot * 2 + 0) * q.rpad + 4 * jq + u] = ar[u];
+      red[(slot * 2 + 1) * q.rpad + 4 * jq + u] = ai[u];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * q.rpad; t += 256) {
+    const int comp = t / q.rpad, j = t % q.rpad;
+    float sum = 0.f;
+    for (int sl = 0; sl < rpr; ++sl) sum += red[(sl * 2 + comp) * q.rpad + j];
+    part[q.part + ((int64_t)it.chunk * 2 + comp) * q.rpad + j] = sum;
   }
 }
 
@@ -1140,7 +1161,7 @@ __global__ void __launch_bounds__(256) k_rzadd(const RSig *sigs, const RItem *it
   for (int t = threadIdx.x; t < 2 * RC_RMAX; t += blockDim.x) {
     const int c = t / RC_RMAX, j = t % RC_RMAX;
     const float v = acoef[((int64_t)it.sig * 2) * RC_RMAX + t];
-    const bool o = rs_odd(q, j);
+    const bool o = (__ldg(&sigs[it.sig].odd[j >> 5]) >> (j & 31)) & 1u;
     as[c][0][j] = o ? 0.f : v;
     as[c][1][j] = o ? v : 0.f;
   }
