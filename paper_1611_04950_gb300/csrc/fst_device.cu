@@ -925,7 +925,8 @@ struct DevRunner : Runner {
     const int64_t rows = a.cplx ? 2 * a.batch : a.batch;
     const int ng = za_groups(rows), ns = ZA_THREADS / ng;
     const int64_t nrb = (rows + ng * ZA_RG - 1) / (ng * ZA_RG);
-    const int64_t blocks = nrb * ((a.N + ns - 1) / ns);
+    const int64_t blocks = nrb * ((a.N + ZA_SPAN - 1) / ZA_SPAN);
+    (void)ns;
     if (blocks >= (1LL << 31)) return fail(FST_EINVAL, "batch too large for the correction pass");
     PROF("k_zadd", a.npairs, (k_zadd<<<(unsigned)blocks, ZA_THREADS, za_smem(a.rpad, ng), cur>>>(a)));
     LAUNCHED("k_zadd");

@@ -870,8 +870,10 @@ __global__ void __launch_bounds__(ZR_THREADS) k_z_rmw(const ConvArgs<float> a, c
 // broadcasts).  Thread (sample i, row group g) keeps ZA_RG sums in registers: per 4 j, one
 // float4 of S and ZA_RG / 4 float4 of a feed 4 ZA_RG FMAs.  Then the sums are added into out
 // (coalesced along the samples).
-// 1-D grid of ceil(N / ns) x (row blocks) blocks, block b = sample block b / nrb, row block
-// b % nrb: the row blocks of the same samples run side by side, so their S_T rows come from L2.
+// A block walks ng such sample blocks (ZA_THREADS samples in all) with its a rows staged once.
+// 1-D grid of ceil(N / ZA_THREADS) x (row blocks) blocks, block b = sample range b / nrb, row
+// block b % nrb: the row blocks of the same samples run side by side, so their S_T rows come
+// from L2.
 // ---------------------------------------------------------------------------
 constexpr int ZA_THREADS = 256, ZA_RG = 16, ZA_ROWS = 128;
 // row groups per block: ceil(rows / 16) rounded up to a power of two, at most 8, so that
@@ -884,6 +886,7 @@ __host__ __device__ inline int za_groups(int64_t rows) {
 __host__ __device__ inline int za_smem(int rpad, int ng) {
   return ((ZA_THREADS / ng) * (rpad + 4) + rpad * (ng * ZA_RG + 4)) * 4;
 }
+constexpr int ZA_SPAN = ZA_THREADS;   // samples per block (ng sub-blocks of ZA_THREADS / ng)
 
 __global__ void __launch_bounds__(ZA_THREADS) k_zadd(const ConvArgs<float> a) {
   extern __shared__ __align__(16) float zsm[];
@@ -895,58 +898,63 @@ __global__ void __launch_bounds__(ZA_THREADS) k_zadd(const ConvArgs<float> a) {
   const int64_t nrb = (rows + brows - 1) / brows;
   const int64_t row0 = ((int64_t)blockIdx.x % nrb) * brows;
   const int nrow = (int)(rows - row0 < brows ? rows - row0 : brows);
-  const int64_t n0 = ((int64_t)blockIdx.x / nrb) * ns;
-  // S_T rows n0 .. n0 + ns - 1 (zero past N)
-  for (int e = threadIdx.x; e < ns * (rpad / 4); e += ZA_THREADS) {
-    const int i = e / (rpad / 4), q = e % (rpad / 4);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (n0 + i < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.ST + (n0 + i) * rpad) + q);
-    *reinterpret_cast<float4 *>(st + i * sst + 4 * q) = v;
-  }
   // a rows of this block, transposed: as[j][row]
   for (int e = threadIdx.x; e < rpad * brows; e += ZA_THREADS) {
     const int rr = e / rpad, j = e % rpad;
     as[j * ast + rr] = (rr < nrow && j < a.r) ? a.acoef[(row0 + rr) * rpad + j] : 0.f;
   }
-  __syncthreads();
   const int i = threadIdx.x % ns, g = threadIdx.x / ns;
-  const int64_t n = n0 + i;
-  float acc[ZA_RG];
-#pragma unroll
-  for (int q = 0; q < ZA_RG; ++q) acc[q] = 0.f;
-  const float *srow = st + i * sst;
-  const float *acol = as + g * ZA_RG;
-  for (int j = 0; j < rpad; j += 4) {
-    const float4 s4 = *reinterpret_cast<const float4 *>(srow + j);
-#pragma unroll
-    for (int q = 0; q < ZA_RG; q += 4) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(acol + (j + 0) * ast + q);
-      const float4 a1 = *reinterpret_cast<const float4 *>(acol + (j + 1) * ast + q);
-      const float4 a2 = *reinterpret_cast<const float4 *>(acol + (j + 2) * ast + q);
-      const float4 a3 = *reinterpret_cast<const float4 *>(acol + (j + 3) * ast + q);
-      acc[q + 0] = fmaf(s4.w, a3.x, fmaf(s4.z, a2.x, fmaf(s4.y, a1.x, fmaf(s4.x, a0.x, acc[q + 0]))));
-      acc[q + 1] = fmaf(s4.w, a3.y, fmaf(s4.z, a2.y, fmaf(s4.y, a1.y, fmaf(s4.x, a0.y, acc[q + 1]))));
-      acc[q + 2] = fmaf(s4.w, a3.z, fmaf(s4.z, a2.z, fmaf(s4.y, a1.z, fmaf(s4.x, a0.z, acc[q + 2]))));
-      acc[q + 3] = fmaf(s4.w, a3.w, fmaf(s4.z, a2.w, fmaf(s4.y, a1.w, fmaf(s4.x, a0.w, acc[q + 3]))));
+  for (int sub = 0; sub < ng; ++sub) {
+    const int64_t n0 = ((int64_t)blockIdx.x / nrb) * ZA_SPAN + (int64_t)sub * ns;
+    if (n0 >= a.N) break;
+    if (sub > 0) __syncthreads();   // the previous sub-block's S rows are no longer read
+    // S_T rows n0 .. n0 + ns - 1 (zero past N)
+    for (int e = threadIdx.x; e < ns * (rpad / 4); e += ZA_THREADS) {
+      const int ii = e / (rpad / 4), q = e % (rpad / 4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n0 + ii < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.ST + (n0 + ii) * rpad) + q);
+      *reinterpret_cast<float4 *>(st + ii * sst + 4 * q) = v;
     }
-  }
-  if (n >= a.N) return;
-  if (!a.cplx) {
+    __syncthreads();
+    const int64_t n = n0 + i;
+    float acc[ZA_RG];
 #pragma unroll
-    for (int q = 0; q < ZA_RG; ++q) {
-      const int rr = g * ZA_RG + q;
-      if (rr < nrow) a.out[(row0 + rr) * a.ld + n] += acc[q];
+    for (int q = 0; q < ZA_RG; ++q) acc[q] = 0.f;
+    const float *srow = st + i * sst;
+    const float *acol = as + g * ZA_RG;
+    for (int j = 0; j < rpad; j += 4) {
+      const float4 s4 = *reinterpret_cast<const float4 *>(srow + j);
+#pragma unroll
+      for (int q = 0; q < ZA_RG; q += 4) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(acol + (j + 0) * ast + q);
+        const float4 a1 = *reinterpret_cast<const float4 *>(acol + (j + 1) * ast + q);
+        const float4 a2 = *reinterpret_cast<const float4 *>(acol + (j + 2) * ast + q);
+        const float4 a3 = *reinterpret_cast<const float4 *>(acol + (j + 3) * ast + q);
+        acc[q + 0] = fmaf(s4.w, a3.x, fmaf(s4.z, a2.x, fmaf(s4.y, a1.x, fmaf(s4.x, a0.x, acc[q + 0]))));
+        acc[q + 1] = fmaf(s4.w, a3.y, fmaf(s4.z, a2.y, fmaf(s4.y, a1.y, fmaf(s4.x, a0.y, acc[q + 1]))));
+        acc[q + 2] = fmaf(s4.w, a3.z, fmaf(s4.z, a2.z, fmaf(s4.y, a1.z, fmaf(s4.x, a0.z, acc[q + 2]))));
+        acc[q + 3] = fmaf(s4.w, a3.w, fmaf(s4.z, a2.w, fmaf(s4.y, a1.w, fmaf(s4.x, a0.w, acc[q + 3]))));
+      }
     }
-  } else {
+    if (n < a.N) {
+      if (!a.cplx) {
 #pragma unroll
-    for (int q = 0; q < ZA_RG; q += 2) {
-      const int rr = g * ZA_RG + q;
-      if (rr < nrow) {
-        float2 *o = reinterpret_cast<float2 *>(a.out) + ((row0 + rr) >> 1) * a.ld + n;
-        float2 v = *o;
-        v.x += acc[q];
-        v.y += acc[q + 1];
-        *o = v;
+        for (int q = 0; q < ZA_RG; ++q) {
+          const int rr = g * ZA_RG + q;
+          if (rr < nrow) a.out[(row0 + rr) * a.ld + n] += acc[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < ZA_RG; q += 2) {
+          const int rr = g * ZA_RG + q;
+          if (rr < nrow) {
+            float2 *o = reinterpret_cast<float2 *>(a.out) + ((row0 + rr) >> 1) * a.ld + n;
+            float2 v = *o;
+            v.x += acc[q];
+            v.y += acc[q + 1];
+            *o = v;
+          }
+        }
       }
     }
   }
