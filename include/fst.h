@@ -226,8 +226,11 @@ fst_status fst_plan_many(fst_plan_t *out, int64_t count, const int64_t *N, const
  * fst_project_ragged -- P_fast y_i for a ragged batch: signal i (device pointer
  * y[i], N_i samples of plans[i]) is projected into out[i] with its own plan.
  * Signals whose transform fits one CTA (FP32 N <= 8192, FP64 N <= 4096) go through
- * one launch per FFT length with per-signal descriptors; longer ones through their
- * plan's four-step path.  The first call with a given (plans, y, out, dtype)
+ * one launch per FFT length with per-signal descriptors.  Longer FP32 signals run as
+ * batches per FFT length through the four-step kernels (real signals two to a complex
+ * transform, each with its own spectrum), with the rank-r corrections of all of them in
+ * two launches; longer FP64 signals run one four-step call each.  y[i] == out[i] (in
+ * place) is allowed.  The first call with a given (plans, y, out, dtype)
  * signature runs directly and allocates; the second records the whole batch in a
  * CUDA graph on a private stream; later calls replay it on `stream` (set
  * FST_GRAPHS=0 in the environment to always launch directly).  Calls with
@@ -242,8 +245,9 @@ fst_status fst_project_ragged(const fst_plan_t *plans, const void *const *y, voi
 /*
  * fst_ragged_tuning -- the launch grouping the autotuner chose for the four-step signals of
  * a ragged batch, for the (plans, y, out, dtype) signature of an earlier fst_project_ragged
- * call: pairs[lg] = signals per launch group of the length class with FFT length 2^lg (0 if
- * the batch has no four-step signal of that length), ms[lg] (may be NULL) = the measured
+ * call: pairs[lg] = transform slots per launch group of the length class with FFT length
+ * 2^lg (a slot holds one complex or two real signals; 0 if the batch has no four-step signal
+ * of that length), ms[lg] (may be NULL) = the measured
  * device time of that class with the chosen grouping (0 when no timing ran).  Both arrays
  * have 32 entries.  The first call of a signature times groupings of 16 to 256 MiB of
  * intermediate per class and keeps the fastest (FST_AUTOTUNE=0 in the environment: 128 MiB,
@@ -318,13 +322,15 @@ unsigned long long fst_noalloc_scratch_bytes(void);
  * Launch accounting, for benchmarks (not part of the method).
  * fst_launch_count   -- number of kernels this process has launched through the
  *                       library so far (plan-time and apply kernels).
- * fst_profile_enable -- on != 0: from now on, every apply-kernel launch is
- *                       bracketed by CUDA events on its stream; clears earlier
- *                       records.  on == 0 stops recording (and clears).
+ * fst_profile_enable -- on != 0: from now on, every apply-kernel launch and the
+ *                       plan-time eigen kernels (bisection, inverse iteration,
+ *                       expansion) are bracketed by CUDA events on their stream;
+ *                       clears earlier records.  on == 0 stops recording (and clears).
  * fst_profile_count  -- number of recorded launches.
  * fst_profile_read   -- record i: kernel name (static string), elapsed device time
  *                       in ms between its events (waits for them), and the number
- *                       of signal pairs it processed.  FST_EINVAL if i is out of range.
+ *                       of signal pairs (eigen kernels: eigenvectors) it processed.
+ *                       FST_EINVAL if i is out of range.
  */
 long long fst_launch_count(void);
 fst_status fst_profile_enable(int on);

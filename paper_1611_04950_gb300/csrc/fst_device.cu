@@ -457,6 +457,7 @@ static fst_status set_attrs() {
   CU(cudaFuncSetAttribute(k_corr_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, cc_smem(64)), "attr");
   CU(cudaFuncSetAttribute(k_zadd, cudaFuncAttributeMaxDynamicSharedMemorySize, za_smem(64, 1)), "attr");
   CU(cudaFuncSetAttribute(k_fastB8192, cudaFuncAttributeMaxDynamicSharedMemorySize, fastb8192_smem()), "attr");
+  CU(cudaFuncSetAttribute(k_fastB4096_2s, cudaFuncAttributeMaxDynamicSharedMemorySize, fastb2s_smem()), "attr");
   CU(cudaFuncSetAttribute(k_colA<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(2)), "attr");
   CU(cudaFuncSetAttribute(k_colA<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(4)), "attr");
   CU(cudaFuncSetAttribute(k_colA<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(8)), "attr");
@@ -506,6 +507,14 @@ static void prof_end(cudaStream_t s, cudaEvent_t ea) {
     prof_begin(cur, name, (units), &_ea);    \
     launch;                                  \
     prof_end(cur, _ea);                      \
+  } while (0)
+
+#define PROF_S(stream, name, units, launch) \
+  do {                                       \
+    cudaEvent_t _ea;                         \
+    prof_begin(stream, name, (units), &_ea); \
+    launch;                                  \
+    prof_end(stream, _ea);                   \
   } while (0)
 
 bool profiling_enabled() { return g_prof_on != 0; }
@@ -830,6 +839,15 @@ struct DevRunner : Runner {
       return FST_OK;
     }
     if (!(L.fast || L.big) || L.log2Q != 12) return passB_t(a, L);
+    if (a.two_spec) {
+      if (!a.rp || a.cplx || a.mode != MODE_CONV)
+        return fail(FST_EINVAL, "two-spectrum row pass needs real ragged slots");
+      TRY(set_attrs());
+      dim3 grid((unsigned)((1u << L.log2P) / 2 + 1), (unsigned)a.npairs);
+      PROF("k_fastB4096_2s", a.npairs, (k_fastB4096_2s<<<grid, 256, fastb2s_smem(), cur>>>(a)));
+      LAUNCHED("k_fastB4096_2s");
+      return FST_OK;
+    }
     dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
     PROF("k_fastB4096", a.npairs, (k_fastB4096<<<grid, 256, 0, cur>>>(a)));
     LAUNCHED("k_fastB4096");
@@ -925,8 +943,7 @@ struct DevRunner : Runner {
     const int64_t rows = a.cplx ? 2 * a.batch : a.batch;
     const int ng = za_groups(rows), ns = ZA_THREADS / ng;
     const int64_t nrb = (rows + ng * ZA_RG - 1) / (ng * ZA_RG);
-    const int64_t blocks = nrb * ((a.N + ZA_SPAN - 1) / ZA_SPAN);
-    (void)ns;
+    const int64_t blocks = nrb * ((a.N + ns - 1) / ns);
     if (blocks >= (1LL << 31)) return fail(FST_EINVAL, "batch too large for the correction pass");
     PROF("k_zadd", a.npairs, (k_zadd<<<(unsigned)blocks, ZA_THREADS, za_smem(a.rpad, ng), cur>>>(a)));
     LAUNCHED("k_zadd");
@@ -978,39 +995,36 @@ struct DevRunner : Runner {
 
   fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
                     double pivmin, double *out, int *flag) override {
-    k_bisect<<<nt, BISECT_THREADS, 0, s>>>(d, e2, n, targets, glo, ghi, pivmin, out, flag);
+    PROF_S(s, "k_bisect", nt, (k_bisect<<<nt, BISECT_THREADS, 0, s>>>(d, e2, n, targets, glo, ghi, pivmin, out, flag)));
     LAUNCHED("k_bisect");
     return FST_OK;
   }
   fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
                    double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
-    k_invit<<<(nt + 31) / 32, 32, 0, s>>>(d, e, n, sigma, nt, tol, iters, x, fd, fdl, fdu, fdu2, piv);
+    PROF_S(s, "k_invit", nt, (k_invit<<<(nt + 31) / 32, 32, 0, s>>>(d, e, n, sigma, nt, tol, iters, x, fd, fdl, fdu, fdu2, piv)));
     LAUNCHED("k_invit");
     return FST_OK;
   }
   fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
-    k_finalize<<<nt, 256, 0, s>>>(x, n, nt, parity, N, S);
+    PROF_S(s, "k_finalize", nt, (k_finalize<<<nt, 256, 0, s>>>(x, n, nt, parity, N, S)));
     LAUNCHED("k_finalize");
     return FST_OK;
   }
   fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
                          int *flag) override {
-    k_bisect_many<<<(nt + 127) / 128, 128, 0, s>>>(td, nt, dcat, e2cat, theta, flag);
+    PROF_S(s, "k_bisect_many", nt, (k_bisect_many<<<(nt + 127) / 128, 128, 0, s>>>(td, nt, dcat, e2cat, theta, flag)));
     LAUNCHED("k_bisect_many");
-    ++g_launches;
     return FST_OK;
   }
   fst_status invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat, const double *theta,
                         double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
-    k_invit_many<<<(nt + 63) / 64, 64, 0, s>>>(td, nt, dcat, ecat, theta, x, fd, fdl, fdu, fdu2, piv);
+    PROF_S(s, "k_invit_many", nt, (k_invit_many<<<(nt + 63) / 64, 64, 0, s>>>(td, nt, dcat, ecat, theta, x, fd, fdl, fdu, fdu2, piv)));
     LAUNCHED("k_invit_many");
-    ++g_launches;
     return FST_OK;
   }
   fst_status finalize_many(const TargetDesc *td, int nt, const double *x) override {
-    k_finalize_many<<<nt, 256, 0, s>>>(td, x);
+    PROF_S(s, "k_finalize_many", nt, (k_finalize_many<<<nt, 256, 0, s>>>(td, x)));
     LAUNCHED("k_finalize_many");
-    ++g_launches;
     return FST_OK;
   }
   fst_status dot(const double *a, const double *b, int64_t N, int nvec, double *out) override {

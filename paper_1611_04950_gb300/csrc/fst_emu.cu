@@ -72,6 +72,7 @@ struct EmuRunner : Runner {
     return FST_OK;
   }
   template <typename T> fst_status passB_t(const ConvArgs<T> &a, const Layout &L) {
+    if (a.two_spec) return FST_EUNSUPPORTED;   // two-spectrum ragged slots run on the device only
     std::vector<unsigned char> smem(L.smem_B + 64);
     c2<T> *buf = reinterpret_cast<c2<T> *>(smem.data());
     for (int64_t pl = 0; pl < a.npairs; ++pl)

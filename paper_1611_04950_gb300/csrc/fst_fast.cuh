@@ -359,11 +359,80 @@ __global__ void __launch_bounds__(FAST_THREADS, 3) k_fastA(const FastArgs f) {
 // ---------------------------------------------------------------------------
 // x[t] times W^{k t} (t = 1..15) from a [t][ldk] table (conjugated for the inverse):
 // lanes with consecutive k read consecutive entries
+// (COHERENT: plain loads, which the compiler keeps between the barriers around them; read-only
+// cache loads may be hoisted over a whole transform and then spill in a kernel with several)
+template <bool COHERENT = false>
 __device__ __forceinline__ void tw_table16(const float2 *tab, int ldk, int k, bool inv, float2 *x) {
 #pragma unroll
   for (int t = 1; t < 16; ++t) {
-    const float2 w = __ldg(tab + t * ldk + k);
+    const float2 w = COHERENT ? tab[t * ldk + k] : __ldg(tab + t * ldk + k);
     x[t] = inv ? make_float2(x[t].x * w.x + x[t].y * w.y, x[t].y * w.x - x[t].x * w.y) : cmul(x[t], w);
+  }
+}
+
+// 4096-point row transforms with 256 threads x 16 values (buf: padded_size(4096) float2 of
+// scratch; every thread of the block calls these, they contain barriers)
+//   row4096_fwd: forward DFT of `row` (global) -> x[t] = X[j + 256 t] (natural order)
+//   row4096_inv: inverse DFT of x[t] = Z[j + 256 t] -> x[t] = z[j + 256 t]
+//   row4096_store: row[j + 256 t] = x[t] W_M^{-n2 k1}, n2 = j + 256 t
+template <bool COHERENT = false>
+__device__ __forceinline__ void row4096_fwd(const float2 *row, float2 *buf, const float2 *twB, int j, float2 *x) {
+  constexpr int T = 256;
+  // stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = row[j + T * t];
+  Dft<float, 16, false>::run(x);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
+  __syncthreads();
+  // stage 2 (Ns = 16)
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_table16<COHERENT>(twB, 16, j & 15, false, x);
+  Dft<float, 16, false>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
+  __syncthreads();
+  // stage 3 (Ns = 256): outputs land at j + 256 t = natural k2
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_table16<COHERENT>(twB + 256, 256, j, false, x);
+  Dft<float, 16, false>::run(x);
+}
+template <bool COHERENT = false>
+__device__ __forceinline__ void row4096_inv(float2 *buf, const float2 *twB, int j, float2 *x) {
+  constexpr int T = 256;
+  // stage 1: its inputs x[j + 256 t] are already in registers
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_table16<COHERENT>(twB, 16, j & 15, true, x);
+  Dft<float, 16, true>::run(x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
+  tw_table16<COHERENT>(twB + 256, 256, j, true, x);
+  Dft<float, 16, true>::run(x);
+}
+__device__ __forceinline__ void row4096_store(float2 *row, const Tw<float> &tw, int log2M, int k1, int j,
+                                              const float2 *x) {
+  constexpr int T = 256;
+  const float2 wj = tw.root<true>((uint64_t)j * (uint64_t)k1, log2M);
+  const float2 wstep = tw.root<true>((uint64_t)T * (uint64_t)k1, log2M);
+  float2 wt = wj;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    row[j + T * t] = cmul(x[t], wt);
+    if (t == 7) wt = cmul(wj, tw.root<true>((uint64_t)(8 * T) * (uint64_t)k1, log2M));
+    else wt = cmul(wt, wstep);
   }
 }
 
@@ -386,27 +455,7 @@ __global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
     }
   }
   float2 x[16];
-  // forward stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory
-#pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = row[j + T * t];
-  Dft<float, 16, false>::run(x);
-#pragma unroll
-  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
-  __syncthreads();
-  // stage 2 (Ns = 16)
-#pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_table16(a.twB, 16, j & 15, false, x);
-  Dft<float, 16, false>::run(x);
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
-  __syncthreads();
-  // stage 3 (Ns = 256): outputs land at j + 256 t = natural k2
-#pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_table16(a.twB + 256, 256, j, false, x);
-  Dft<float, 16, false>::run(x);
+  row4096_fwd(row, buf, a.twB, j, x);
   if (a.mode == MODE_FORWARD) {
 #pragma unroll
     for (int t = 0; t < 16; ++t) row[j + T * t] = x[t];
@@ -415,34 +464,83 @@ __global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
   const float *sp = spec_of(a, pl) + (int64_t)k1 * Q;
 #pragma unroll
   for (int t = 0; t < 16; ++t) x[t] = cscale(x[t], __ldg(sp + j + T * t));
-  // inverse stage 1: its inputs x[j + 256 t] are already in registers
-  Dft<float, 16, true>::run(x);
-  __syncthreads();
+  row4096_inv(buf, a.twB, j, x);
+  row4096_store(row, a.tw, a.log2M, k1, j, x);
+}
+
+// ---------------------------------------------------------------------------
+// pass B of a ragged slot holding two real signals with different spectra Ca, Cb (their own
+// plans, same FFT length).  With x = ya + i yb, X = FFT(x): Ya = (X[k] + conj X[-k]) / 2,
+// i Yb = (X[k] - conj X[-k]) / 2, so the filtered spectrum Ca Ya + i Cb Yb is
+//   Z[k] = (Ca + Cb)/2 X[k] + (Ca - Cb)/2 conj X[-k],
+// and IFFT(Z) = (B_a ya) + i (B_b yb) (Ca, Cb real and even).  For k = k1 + P k2 the index -k
+// lies in row P - k1, column Q - 1 - k2 (row 0: column (Q - k2) mod Q).  A CTA takes rows
+// r0 = blockIdx.x and r1 = P - r0 (rows 0 and P/2 pair with themselves): both forward
+// transforms land in shared memory, each thread then forms Z for an index and its mirror in
+// place (the map k2 -> Q - 1 - k2 pairs the two buffers one to one), and the two inverse
+// transforms follow one after the other.
+// grid (P/2 + 1, slots), 256 threads, dynamic shared memory 2 padded_size(4096) float2.
+// ---------------------------------------------------------------------------
+constexpr size_t fastb2s_smem() { return 2 * (size_t)padded_size(4096) * sizeof(float2); }
+__device__ __forceinline__ float2 two_spec_z(float2 xk, float2 xm, float ca, float cb) {
+  const float A = 0.5f * (ca + cb), Bm = 0.5f * (ca - cb);
+  return make_float2(A * xk.x + Bm * xm.x, A * xk.y - Bm * xm.y);
+}
+__global__ void __launch_bounds__(256, 3) k_fastB4096_2s(const ConvArgs<float> a) {
+  constexpr int Q = 4096, T = 256;
+  extern __shared__ __align__(16) float2 b2s[];
+  float2 *buf0 = b2s, *buf1 = b2s + padded_size(Q);
+  const int P = 1 << a.log2P;
+  const int r0 = blockIdx.x, r1 = (P - r0) & (P - 1);
+  const int64_t pl = blockIdx.y;
+  const int j = threadIdx.x;
+  const RPair<float> &q = a.rp[a.pair0 + pl];
+  const float *ca = q.spec, *cb = q.spec2 ? q.spec2 : q.spec;
+  float2 *row0 = a.inter + (pl * P + r0) * (int64_t)Q;
+  float2 x[16];
+  row4096_fwd<true>(row0, buf0, a.twB, j, x);
+  __syncthreads();   // the last stage's reads of buf0 are done
 #pragma unroll
-  for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
-  __syncthreads();
+  for (int t = 0; t < 16; ++t) buf0[pad(j + T * t)] = x[t];
+  if (r1 == r0) {
+    __syncthreads();
+    const float *sa = ca + (int64_t)r0 * Q, *sb = cb + (int64_t)r0 * Q;
 #pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_table16(a.twB, 16, j & 15, true, x);
-  Dft<float, 16, true>::run(x);
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < 16; ++t) buf[pad(((j >> 4) << 8) + (j & 15) + 16 * t)] = x[t];
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = buf[pad(j + T * t)];
-  tw_table16(a.twB + 256, 256, j, true, x);
-  Dft<float, 16, true>::run(x);
-  // times W_M^{-n2 k1}, n2 = j + 256 t, straight to global memory
-  const float2 wj = a.tw.root<true>((uint64_t)j * (uint64_t)k1, a.log2M);
-  const float2 wstep = a.tw.root<true>((uint64_t)T * (uint64_t)k1, a.log2M);
-  float2 wt = wj;
-#pragma unroll
-  for (int t = 0; t < 16; ++t) {
-    row[j + T * t] = cmul(x[t], wt);
-    if (t == 7) wt = cmul(wj, a.tw.root<true>((uint64_t)(8 * T) * (uint64_t)k1, a.log2M));
-    else wt = cmul(wt, wstep);
+    for (int t = 0; t < 16; ++t) {
+      const int k2 = j + T * t;
+      const int m = (r0 == 0) ? ((Q - k2) & (Q - 1)) : (Q - 1 - k2);
+      x[t] = two_spec_z(x[t], buf0[pad(m)], __ldg(sa + k2), __ldg(sb + k2));
+    }
+    row4096_inv<true>(buf0, a.twB, j, x);   // begins with a barrier: every mirror read is done
+    row4096_store(row0, a.tw, a.log2M, r0, j, x);
+    return;
   }
+  float2 *row1 = a.inter + (pl * P + r1) * (int64_t)Q;
+  row4096_fwd<true>(row1, buf1, a.twB, j, x);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) buf1[pad(j + T * t)] = x[t];
+  __syncthreads();
+  {
+    const float *sa0 = ca + (int64_t)r0 * Q, *sb0 = cb + (int64_t)r0 * Q;
+    const float *sa1 = ca + (int64_t)r1 * Q, *sb1 = cb + (int64_t)r1 * Q;
+#pragma unroll 4
+    for (int t = 0; t < 16; ++t) {
+      const int k2 = j + T * t, m = Q - 1 - k2;
+      const float2 x0 = buf0[pad(k2)], x1 = buf1[pad(m)];
+      buf0[pad(k2)] = two_spec_z(x0, x1, __ldg(sa0 + k2), __ldg(sb0 + k2));
+      buf1[pad(m)] = two_spec_z(x1, x0, __ldg(sa1 + m), __ldg(sb1 + m));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf0[pad(j + T * t)];
+  row4096_inv<true>(buf0, a.twB, j, x);
+  row4096_store(row0, a.tw, a.log2M, r0, j, x);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = buf1[pad(j + T * t)];
+  row4096_inv<true>(buf1, a.twB, j, x);
+  row4096_store(row1, a.tw, a.log2M, r1, j, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -870,10 +968,8 @@ __global__ void __launch_bounds__(ZR_THREADS) k_z_rmw(const ConvArgs<float> a, c
 // broadcasts).  Thread (sample i, row group g) keeps ZA_RG sums in registers: per 4 j, one
 // float4 of S and ZA_RG / 4 float4 of a feed 4 ZA_RG FMAs.  Then the sums are added into out
 // (coalesced along the samples).
-// A block walks ng such sample blocks (ZA_THREADS samples in all) with its a rows staged once.
-// 1-D grid of ceil(N / ZA_THREADS) x (row blocks) blocks, block b = sample range b / nrb, row
-// block b % nrb: the row blocks of the same samples run side by side, so their S_T rows come
-// from L2.
+// 1-D grid of ceil(N / ns) x (row blocks) blocks, block b = sample block b / nrb, row block
+// b % nrb: the row blocks of the same samples run side by side, so their S_T rows come from L2.
 // ---------------------------------------------------------------------------
 constexpr int ZA_THREADS = 256, ZA_RG = 16, ZA_ROWS = 128;
 // row groups per block: ceil(rows / 16) rounded up to a power of two, at most 8, so that
@@ -886,7 +982,6 @@ __host__ __device__ inline int za_groups(int64_t rows) {
 __host__ __device__ inline int za_smem(int rpad, int ng) {
   return ((ZA_THREADS / ng) * (rpad + 4) + rpad * (ng * ZA_RG + 4)) * 4;
 }
-constexpr int ZA_SPAN = ZA_THREADS;   // samples per block (ng sub-blocks of ZA_THREADS / ng)
 
 __global__ void __launch_bounds__(ZA_THREADS) k_zadd(const ConvArgs<float> a) {
   extern __shared__ __align__(16) float zsm[];
@@ -898,63 +993,58 @@ __global__ void __launch_bounds__(ZA_THREADS) k_zadd(const ConvArgs<float> a) {
   const int64_t nrb = (rows + brows - 1) / brows;
   const int64_t row0 = ((int64_t)blockIdx.x % nrb) * brows;
   const int nrow = (int)(rows - row0 < brows ? rows - row0 : brows);
+  const int64_t n0 = ((int64_t)blockIdx.x / nrb) * ns;
+  // S_T rows n0 .. n0 + ns - 1 (zero past N)
+  for (int e = threadIdx.x; e < ns * (rpad / 4); e += ZA_THREADS) {
+    const int i = e / (rpad / 4), q = e % (rpad / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n0 + i < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.ST + (n0 + i) * rpad) + q);
+    *reinterpret_cast<float4 *>(st + i * sst + 4 * q) = v;
+  }
   // a rows of this block, transposed: as[j][row]
   for (int e = threadIdx.x; e < rpad * brows; e += ZA_THREADS) {
     const int rr = e / rpad, j = e % rpad;
     as[j * ast + rr] = (rr < nrow && j < a.r) ? a.acoef[(row0 + rr) * rpad + j] : 0.f;
   }
+  __syncthreads();
   const int i = threadIdx.x % ns, g = threadIdx.x / ns;
-  for (int sub = 0; sub < ng; ++sub) {
-    const int64_t n0 = ((int64_t)blockIdx.x / nrb) * ZA_SPAN + (int64_t)sub * ns;
-    if (n0 >= a.N) break;
-    if (sub > 0) __syncthreads();   // the previous sub-block's S rows are no longer read
-    // S_T rows n0 .. n0 + ns - 1 (zero past N)
-    for (int e = threadIdx.x; e < ns * (rpad / 4); e += ZA_THREADS) {
-      const int ii = e / (rpad / 4), q = e % (rpad / 4);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (n0 + ii < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.ST + (n0 + ii) * rpad) + q);
-      *reinterpret_cast<float4 *>(st + ii * sst + 4 * q) = v;
+  const int64_t n = n0 + i;
+  float acc[ZA_RG];
+#pragma unroll
+  for (int q = 0; q < ZA_RG; ++q) acc[q] = 0.f;
+  const float *srow = st + i * sst;
+  const float *acol = as + g * ZA_RG;
+  for (int j = 0; j < rpad; j += 4) {
+    const float4 s4 = *reinterpret_cast<const float4 *>(srow + j);
+#pragma unroll
+    for (int q = 0; q < ZA_RG; q += 4) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(acol + (j + 0) * ast + q);
+      const float4 a1 = *reinterpret_cast<const float4 *>(acol + (j + 1) * ast + q);
+      const float4 a2 = *reinterpret_cast<const float4 *>(acol + (j + 2) * ast + q);
+      const float4 a3 = *reinterpret_cast<const float4 *>(acol + (j + 3) * ast + q);
+      acc[q + 0] = fmaf(s4.w, a3.x, fmaf(s4.z, a2.x, fmaf(s4.y, a1.x, fmaf(s4.x, a0.x, acc[q + 0]))));
+      acc[q + 1] = fmaf(s4.w, a3.y, fmaf(s4.z, a2.y, fmaf(s4.y, a1.y, fmaf(s4.x, a0.y, acc[q + 1]))));
+      acc[q + 2] = fmaf(s4.w, a3.z, fmaf(s4.z, a2.z, fmaf(s4.y, a1.z, fmaf(s4.x, a0.z, acc[q + 2]))));
+      acc[q + 3] = fmaf(s4.w, a3.w, fmaf(s4.z, a2.w, fmaf(s4.y, a1.w, fmaf(s4.x, a0.w, acc[q + 3]))));
     }
-    __syncthreads();
-    const int64_t n = n0 + i;
-    float acc[ZA_RG];
+  }
+  if (n >= a.N) return;
+  if (!a.cplx) {
 #pragma unroll
-    for (int q = 0; q < ZA_RG; ++q) acc[q] = 0.f;
-    const float *srow = st + i * sst;
-    const float *acol = as + g * ZA_RG;
-    for (int j = 0; j < rpad; j += 4) {
-      const float4 s4 = *reinterpret_cast<const float4 *>(srow + j);
-#pragma unroll
-      for (int q = 0; q < ZA_RG; q += 4) {
-        const float4 a0 = *reinterpret_cast<const float4 *>(acol + (j + 0) * ast + q);
-        const float4 a1 = *reinterpret_cast<const float4 *>(acol + (j + 1) * ast + q);
-        const float4 a2 = *reinterpret_cast<const float4 *>(acol + (j + 2) * ast + q);
-        const float4 a3 = *reinterpret_cast<const float4 *>(acol + (j + 3) * ast + q);
-        acc[q + 0] = fmaf(s4.w, a3.x, fmaf(s4.z, a2.x, fmaf(s4.y, a1.x, fmaf(s4.x, a0.x, acc[q + 0]))));
-        acc[q + 1] = fmaf(s4.w, a3.y, fmaf(s4.z, a2.y, fmaf(s4.y, a1.y, fmaf(s4.x, a0.y, acc[q + 1]))));
-        acc[q + 2] = fmaf(s4.w, a3.z, fmaf(s4.z, a2.z, fmaf(s4.y, a1.z, fmaf(s4.x, a0.z, acc[q + 2]))));
-        acc[q + 3] = fmaf(s4.w, a3.w, fmaf(s4.z, a2.w, fmaf(s4.y, a1.w, fmaf(s4.x, a0.w, acc[q + 3]))));
-      }
+    for (int q = 0; q < ZA_RG; ++q) {
+      const int rr = g * ZA_RG + q;
+      if (rr < nrow) a.out[(row0 + rr) * a.ld + n] += acc[q];
     }
-    if (n < a.N) {
-      if (!a.cplx) {
+  } else {
 #pragma unroll
-        for (int q = 0; q < ZA_RG; ++q) {
-          const int rr = g * ZA_RG + q;
-          if (rr < nrow) a.out[(row0 + rr) * a.ld + n] += acc[q];
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < ZA_RG; q += 2) {
-          const int rr = g * ZA_RG + q;
-          if (rr < nrow) {
-            float2 *o = reinterpret_cast<float2 *>(a.out) + ((row0 + rr) >> 1) * a.ld + n;
-            float2 v = *o;
-            v.x += acc[q];
-            v.y += acc[q + 1];
-            *o = v;
-          }
-        }
+    for (int q = 0; q < ZA_RG; q += 2) {
+      const int rr = g * ZA_RG + q;
+      if (rr < nrow) {
+        float2 *o = reinterpret_cast<float2 *>(a.out) + ((row0 + rr) >> 1) * a.ld + n;
+        float2 v = *o;
+        v.x += acc[q];
+        v.y += acc[q + 1];
+        *o = v;
       }
     }
   }

@@ -1663,8 +1663,10 @@ static bool autotune_enabled() {
 // The four-step signals of a ragged batch (FP32 device plans), by FFT length class M:
 //   1. the correction coefficients a_i = D_i o S_T,i^T y_i of every signal (one launch over
 //      (signal, 2048-sample chunk) items, one reduction launch);
-//   2. per class, launch groups of signals through the batched column / row / column passes
-//      (each signal a pair slot with its own data, length and spectrum), B y only;
+//   2. per class, launch groups of transform slots through the batched column / row / column
+//      passes, B y only: a complex signal takes a slot of its own, real signals share one two at
+//      a time (re, im), each with its own data, length and spectrum (4096-point rows: the row
+//      pass applies both spectra; other row lengths: one real signal per slot);
 //   3. out_i += S_T,i a_i over all items (one launch).
 // The pairs per launch group of each class are picked on the first call (autotuner: the
 // candidate groupings of 16 .. 256 MiB of intermediate are timed with device events and the
@@ -1726,21 +1728,37 @@ static fst_status ragged_fourstep_f32(const fst_plan_t *plans, const void *const
     const int64_t cnt = (int64_t)c.size();
     fst_plan_t p0 = plans[idx[c[0]]];
     int64_t Nmax = 0;
-    std::vector<RPair<float>> rp(cnt);
-    for (int64_t k = 0; k < cnt; ++k) {
-      fst_plan_t p = plans[idx[c[k]]];
-      rp[k].y = (const float *)y[idx[c[k]]];
-      rp[k].out = (float *)out[idx[c[k]]];
-      rp[k].spec = p->spec32;
-      rp[k].N = p->N;
-      Nmax = std::max(Nmax, p->N);
+    for (int k : c) Nmax = std::max(Nmax, plans[idx[k]]->N);
+    const Layout L = make_layout(Nmax, lg, false, 8, true);
+    // real signals of the class travel two to a slot (re, im) when the row pass can apply two
+    // spectra (4096-point rows); otherwise one per slot
+    const bool two = !cplx && (L.fast || L.big) && L.log2Q == 12;
+    const int64_t nslot = two ? (cnt + 1) / 2 : cnt;
+    std::vector<RPair<float>> rp(nslot);
+    for (int64_t k = 0; k < nslot; ++k) {
+      const int i0 = two ? c[2 * k] : c[k];
+      fst_plan_t p = plans[idx[i0]];
+      RPair<float> &q = rp[k];
+      q = RPair<float>{};
+      q.y = (const float *)y[idx[i0]];
+      q.out = (float *)out[idx[i0]];
+      q.spec = p->spec32;
+      q.N = p->N;
+      if (two && 2 * k + 1 < cnt) {
+        const int i1 = c[2 * k + 1];
+        fst_plan_t p1 = plans[idx[i1]];
+        q.y2 = (const float *)y[idx[i1]];
+        q.out2 = (float *)out[idx[i1]];
+        q.spec2 = p1->spec32;
+        q.N2 = p1->N;
+      }
     }
     void *drp;
     TRY(ragged_buf(R, st, rp.size() * sizeof(RPair<float>), rp.data(), &drp));
-    const Layout L = make_layout(Nmax, lg, false, 8, true);
     ConvArgs<float> a{};
     a.rp = (const RPair<float> *)drp;
-    a.batch = cnt;
+    a.two_spec = two ? 1 : 0;
+    a.batch = nslot;
     a.cplx = cplx ? 1 : 0;
     a.N = Nmax;
     a.log2M = L.log2M;
@@ -1757,9 +1775,9 @@ static fst_status ragged_fourstep_f32(const fst_plan_t *plans, const void *const
     a.inter = (float2 *)dws;
     a.mode = MODE_CONV;
     auto run_groups = [&](int64_t chunk) -> fst_status {
-      for (int64_t q0 = 0; q0 < cnt; q0 += chunk) {
+      for (int64_t q0 = 0; q0 < nslot; q0 += chunk) {
         a.pair0 = q0;
-        a.npairs = std::min<int64_t>(chunk, cnt - q0);
+        a.npairs = std::min<int64_t>(chunk, nslot - q0);
         TRY(R->passA(a, L));
         TRY(R->passB(a, L));
         TRY(R->passC(a, L));

@@ -71,13 +71,18 @@ __host__ __device__ inline int64_t spec_pos(const Layout &L, int64_t k) {
 
 
 
-// One signal of a ragged four-step batch (its own plan); it takes a whole pair slot (a real
-// signal travels as the real part, the imaginary part is zero)
+// A pair slot of a ragged four-step batch: one complex signal, or two real signals of the same
+// FFT length with their own plans (the second travels as the imaginary part; y2 == nullptr
+// when the slot holds one real signal)
 template <typename T> struct RPair {
   const T *y;
   T *out;
   const T *spec;   // its spectrum, in the length class's [k1][k2] layout
   int64_t N;
+  const T *y2;     // second real signal of the slot (or nullptr), its output, spectrum, length
+  T *out2;
+  const T *spec2;
+  int64_t N2;
 };
 
 // Rank-r correction of the four-step signals of a ragged batch (FP32 device): one entry per
@@ -133,6 +138,7 @@ template <typename T> struct ConvArgs {
   const float2 *twB;  // FP32 device plans: stage twiddles of the 4096-point row FFT, then W_1024^t
   const float2 *tw8;  // FP32 device plans: stage twiddles of the 8192-point row FFT
   const RPair<T> *rp; // ragged batch: per pair slot signal, length and spectrum (else nullptr)
+  int two_spec;       // ragged real slots hold two signals with their own spectra (pass B pairs rows)
 };
 // twB: [t][k] W_256^{k t} (k, t < 16), [t][k] W_4096^{k t} (t < 16, k < 256), W_1024^t (t < 1024)
 constexpr int TWB_P_OFF = 16 * 16 + 16 * 256;
@@ -171,9 +177,8 @@ template <typename T> FST_HD c2<T> load_pair(const ConvArgs<T> &a, int64_t pl, i
   const int64_t p = a.pair0 + pl;
   if (a.rp) {
     const RPair<T> &q = a.rp[p];
-    if (n >= q.N) return mk<T>(0, 0);
-    if (a.cplx) return reinterpret_cast<const c2<T> *>(q.y)[n];
-    return mk<T>(q.y[n], (T)0);
+    if (a.cplx) return n < q.N ? reinterpret_cast<const c2<T> *>(q.y)[n] : mk<T>(0, 0);
+    return mk<T>(n < q.N ? q.y[n] : (T)0, (q.y2 && n < q.N2) ? q.y2[n] : (T)0);
   }
   if (a.cplx) {
     const c2<T> *y2 = reinterpret_cast<const c2<T> *>(a.y);
@@ -188,9 +193,12 @@ template <typename T> FST_HD void store_pair(const ConvArgs<T> &a, int64_t pl, i
   const int64_t p = a.pair0 + pl;
   if (a.rp) {
     const RPair<T> &q = a.rp[p];
-    if (n >= q.N) return;
-    if (a.cplx) reinterpret_cast<c2<T> *>(q.out)[n] = v;
-    else q.out[n] = v.x;
+    if (a.cplx) {
+      if (n < q.N) reinterpret_cast<c2<T> *>(q.out)[n] = v;
+      return;
+    }
+    if (n < q.N) q.out[n] = v.x;
+    if (q.out2 && n < q.N2) q.out2[n] = v.y;
     return;
   }
   if (a.cplx) {

@@ -122,60 +122,74 @@ struct TargetDesc {
 FST_HD void invit_body(const double *d, const double *e, int n, double sigma, double tol, int iters, int t, int nt,
                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) {
 #define AT(a, i) a[(int64_t)(i) * nt + t]
-  // factor: fd = U diagonal, fdu / fdu2 = U super-diagonals, fdl = multipliers
-  for (int i = 0; i < n; ++i) {
-    AT(fd, i) = ldg(d + i) - sigma;
-    if (i + 1 < n) { AT(fdu, i) = ldg(e + i + 1); AT(fdl, i) = ldg(e + i + 1); }
-    AT(fdu2, i) = 0.0;
-    AT(piv, i) = 0;
-  }
+  // The elimination and both sweeps carry the entries they update from one step to the next in
+  // registers (cd, cu: the current U diagonal and super-diagonal at i; cur: x[i]; x1, x2: x[i+1],
+  // x[i+2]), so each step reads only inputs and the serial chain never waits on a memory round
+  // trip.  Same operations, same order as the textbook in-place form.
+  auto lift = [&](double p) { return (fabs(p) < tol) ? ((p < 0.0) ? -tol : tol) : p; };
+  // factor: fd = U diagonal (zero pivots lifted to tol), fdu / fdu2 = U super-diagonals,
+  // fdl = multipliers
+  double cd = ldg(d) - sigma;
+  double cu = (n > 1) ? ldg(e + 1) : 0.0;
   for (int i = 0; i + 1 < n; ++i) {
-    const double di = AT(fd, i), li = AT(fdl, i);
-    if (fabs(di) >= fabs(li)) {
-      const double f = (di != 0.0) ? li / di : 0.0;
+    const double li = ldg(e + i + 1);
+    const double nd = ldg(d + i + 1) - sigma;
+    const double nu = (i + 2 < n) ? ldg(e + i + 2) : 0.0;
+    if (fabs(cd) >= fabs(li)) {
+      const double f = (cd != 0.0) ? li / cd : 0.0;
       AT(fdl, i) = f;
-      AT(fd, i + 1) = AT(fd, i + 1) - f * AT(fdu, i);
+      AT(fd, i) = lift(cd);
+      AT(fdu, i) = cu;
+      AT(fdu2, i) = 0.0;
+      AT(piv, i) = 0;
+      cd = nd - f * cu;
+      cu = nu;
     } else {
-      const double f = di / li;
-      AT(fd, i) = li;
+      const double f = cd / li;
       AT(fdl, i) = f;
-      const double tmp = AT(fdu, i);
-      AT(fdu, i) = AT(fd, i + 1);
-      AT(fd, i + 1) = tmp - f * AT(fd, i + 1);
-      if (i + 2 < n) {
-        AT(fdu2, i) = AT(fdu, i + 1);
-        AT(fdu, i + 1) = -f * AT(fdu, i + 1);
-      }
+      AT(fd, i) = lift(li);
+      AT(fdu, i) = nd;
+      AT(fdu2, i) = (i + 2 < n) ? nu : 0.0;
       AT(piv, i) = 1;
+      cd = cu - f * nd;
+      cu = (i + 2 < n) ? -f * nu : 0.0;
     }
   }
-  for (int i = 0; i < n; ++i) {
-    const double p = AT(fd, i);
-    if (fabs(p) < tol) AT(fd, i) = (p < 0.0) ? -tol : tol;
-  }
+  AT(fd, n - 1) = lift(cd);
+  AT(fdu, n - 1) = 0.0;
+  AT(fdl, n - 1) = 0.0;
+  AT(fdu2, n - 1) = 0.0;
+  AT(piv, n - 1) = 0;
   // start vector: deterministic, no structure shared with any eigenvector
   for (int i = 0; i < n; ++i) {
     const double g = (double)i * 0.6180339887498949;
     AT(x, i) = 0.5 + (g - floor(g));
   }
   for (int it = 0; it < iters; ++it) {
+    // L solve with the row interchanges
+    double cur = AT(x, 0);
     for (int i = 0; i + 1 < n; ++i) {
+      const double nx = AT(x, i + 1), l = AT(fdl, i);
       if (AT(piv, i) == 0) {
-        AT(x, i + 1) = AT(x, i + 1) - AT(fdl, i) * AT(x, i);
+        AT(x, i) = cur;
+        cur = nx - l * cur;
       } else {
-        const double tmp = AT(x, i);
-        AT(x, i) = AT(x, i + 1);
-        AT(x, i + 1) = tmp - AT(fdl, i) * AT(x, i);
+        AT(x, i) = nx;
+        cur = cur - l * nx;
       }
     }
-    double mx = 0.0;
+    AT(x, n - 1) = cur;
+    // U solve, max-norm
+    double mx = 0.0, x1 = 0.0, x2 = 0.0;
     for (int i = n - 1; i >= 0; --i) {
       double v = AT(x, i);
-      if (i + 1 < n) v -= AT(fdu, i) * AT(x, i + 1);
-      if (i + 2 < n) v -= AT(fdu2, i) * AT(x, i + 2);
+      if (i + 1 < n) v -= AT(fdu, i) * x1;
+      if (i + 2 < n) v -= AT(fdu2, i) * x2;
       v /= AT(fd, i);
       AT(x, i) = v;
       mx = fmax(mx, fabs(v));
+      x2 = x1;
+      x1 = v;
     }
     const double s = (mx > 0.0) ? 1.0 / mx : 1.0;
     for (int i = 0; i < n; ++i) AT(x, i) = AT(x, i) * s;

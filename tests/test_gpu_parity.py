@@ -486,6 +486,35 @@ def test_ragged_batch_against_oracle_and_replay():
         assert err < 1e-5, (i, N, err)
 
 
+@pytest.mark.parametrize("inplace", [False, True])
+def test_ragged_paired_real_slots(inplace):
+    # real signals of one FFT-length class share a complex transform two at a time, each with
+    # its own spectrum (different N, W, eps); an odd count leaves one slot with a single signal.
+    # M = 2^18 (P = 64, two-stage column passes) and M = 2^16 (P = 16): every signal against
+    # the FP64 oracle, and the in-place call equal to the out-of-place one
+    dev = _cuda()
+    params = [(70001, 0.3, 1e-6), (90000, 0.05, 1e-4), (100003, 0.12, 1e-8), (120000, 0.2, 1e-6),
+              (131072, 0.01, 1e-3), (20000, 0.25, 1e-6), (30001, 0.1, 1e-8), (32768, 0.03, 1e-4)]
+    ps = F.PlanSet(params)
+    rng = np.random.default_rng(21)
+    ys64 = [rng.standard_normal(N) for (N, W, e) in params]
+    ys = [torch.as_tensor(y, dtype=torch.float32, device=dev) for y in ys64]
+    outs = [torch.empty_like(v) for v in ys]
+    ps.project(ys, outs)
+    if inplace:
+        io = [v.clone() for v in ys]
+        ps.project(io, io)
+        torch.cuda.synchronize()
+        for a, b in zip(outs, io):
+            assert torch.equal(a, b)
+    torch.cuda.synchronize()
+    for i, (N, W, e) in enumerate(params):
+        op = oplan(N, W, O.default_K(N, W), e)
+        ref = O.fast_project(op, ys64[i])
+        err = np.linalg.norm(outs[i].double().cpu().numpy() - ref) / np.linalg.norm(ys64[i])
+        assert err < 1e-5, (i, N, err)
+
+
 def test_ragged_4096_every_signal():
     # the ragged workload at full size (4096 signals, N log-uniform in [1000, 262144], own W and
     # eps each): every signal of the batched call against the one-signal-per-call path, a
