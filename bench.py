@@ -250,7 +250,7 @@ def run_ragged_bench(args):
     launches = F.fst_launch_count() - l0
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    tuning = {f"M=2^{lg}": {"signals_per_group": n, "ms": t} for lg, (n, t) in ps.tuning(ys, outs).items()}
+    tuning = {f"M=2^{lg}": {"slots_per_group": n, "ms": t} for lg, (n, t) in ps.tuning(ys, outs).items()}
     # per-kernel device time of one batched call (events around every launch: direct launches)
     F.fst_profile_enable(True)
     ps.project(ys, outs)

@@ -129,24 +129,13 @@ template <typename T> __global__ void __launch_bounds__(1024) k_passC(const Conv
 // plan kernels
 // ---------------------------------------------------------------------------
 
-__global__ void k_bisect(const double *d, const double *e2, int n, const int *targets, double glo, double ghi,
-                         double pivmin, double *out, int *flag) {
+__global__ void k_bisect_ms_many(const TargetDesc *td, const double *dcat, const double *e2cat, double *theta,
+                                 int *flag) {
   __shared__ BisectShared sh;
   DevExPlan ex;
-  bisect_body(ex, d, e2, n, targets[blockIdx.x], glo, ghi, pivmin, out + blockIdx.x, flag, &sh);
-}
-
-__global__ void k_invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
-                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
-  invit_body(d, e, n, sigma[t], tol, iters, t, nt, x, fd, fdl, fdu, fdu2, piv);
-}
-
-__global__ void k_finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) {
-  __shared__ double sh[2 * 256];
-  DevExPlan ex;
-  finalize_body(ex, x, n, nt, (int)blockIdx.x, parity, N, S + (int64_t)blockIdx.x * N, sh);
+  const TargetDesc q = td[blockIdx.x];
+  bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + blockIdx.x,
+              flag, &sh);
 }
 
 __global__ void k_bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
@@ -993,26 +982,17 @@ struct DevRunner : Runner {
   }
   fst_status passC(const ConvArgs<double> &a, const Layout &L) override { return passC_t(a, L); }
 
-  fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
-                    double pivmin, double *out, int *flag) override {
-    PROF_S(s, "k_bisect", nt, (k_bisect<<<nt, BISECT_THREADS, 0, s>>>(d, e2, n, targets, glo, ghi, pivmin, out, flag)));
-    LAUNCHED("k_bisect");
-    return FST_OK;
-  }
-  fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
-                   double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
-    PROF_S(s, "k_invit", nt, (k_invit<<<(nt + 31) / 32, 32, 0, s>>>(d, e, n, sigma, nt, tol, iters, x, fd, fdl, fdu, fdu2, piv)));
-    LAUNCHED("k_invit");
-    return FST_OK;
-  }
-  fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
-    PROF_S(s, "k_finalize", nt, (k_finalize<<<nt, 256, 0, s>>>(x, n, nt, parity, N, S)));
-    LAUNCHED("k_finalize");
+  fst_status bisect_ms_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
+                            int *flag) override {
+    if (nt <= 0) return FST_OK;
+    PROF_S(s, "k_bisect_ms_many", nt, (k_bisect_ms_many<<<nt, BISECT_THREADS, 0, s>>>(td, dcat, e2cat, theta, flag)));
+    LAUNCHED("k_bisect_ms_many");
     return FST_OK;
   }
   fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
                          int *flag) override {
-    PROF_S(s, "k_bisect_many", nt, (k_bisect_many<<<(nt + 127) / 128, 128, 0, s>>>(td, nt, dcat, e2cat, theta, flag)));
+    // one warp per block: the targets spread over every SM (each one's FP64 pipe is the limit)
+    PROF_S(s, "k_bisect_many", nt, (k_bisect_many<<<(nt + 31) / 32, 32, 0, s>>>(td, nt, dcat, e2cat, theta, flag)));
     LAUNCHED("k_bisect_many");
     return FST_OK;
   }

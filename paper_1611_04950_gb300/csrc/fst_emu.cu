@@ -131,25 +131,14 @@ struct EmuRunner : Runner {
   fst_status passC(const ConvArgs<float> &a, const Layout &L) override { return passC_t(a, L); }
   fst_status passC(const ConvArgs<double> &a, const Layout &L) override { return passC_t(a, L); }
 
-  fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo, double ghi,
-                    double pivmin, double *out, int *flag) override {
+  fst_status bisect_ms_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat, double *theta,
+                            int *flag) override {
     for (int t = 0; t < nt; ++t) {
+      const TargetDesc &q = td[t];
       BisectShared sh;
       HostEx<NoStateH> ex(BISECT_THREADS);
-      bisect_body(ex, d, e2, n, targets[t], glo, ghi, pivmin, out + t, flag, &sh);
-    }
-    return FST_OK;
-  }
-  fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol, int iters,
-                   double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) override {
-    for (int t = 0; t < nt; ++t) invit_body(d, e, n, sigma[t], tol, iters, t, nt, x, fd, fdl, fdu, fdu2, piv);
-    return FST_OK;
-  }
-  fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) override {
-    std::vector<double> sh(2 * 256);
-    for (int t = 0; t < nt; ++t) {
-      HostEx<NoStateH> ex(256);
-      finalize_body(ex, x, n, nt, t, parity, N, S + (int64_t)t * N, sh.data());
+      bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag,
+                  &sh);
     }
     return FST_OK;
   }

@@ -531,67 +531,117 @@ static fst_status window_eigenvalues(fst_plan_t p, double *S, int nwin, double *
 
 // Slepian vectors s^(l), lo <= l <= hi, as rows S[l - lo][0..N), and their
 // eigenvalues lambda_l = s^T B s (FP64 FFT convolution with spec64 = DFT_M(c)/M).
-static fst_status window_vectors(fst_plan_t p, Scoped &sc, int64_t lo, int64_t hi, double *S, double *lam_host,
-                                 const double *spec_unit) {
-  Runner *R = p->R;
-  const int64_t N = p->N;
-  const int nwin = (int)(hi - lo + 1);
-  for (int parity = 0; parity < 2; ++parity) {
-    Reduced red = reduced_tridiagonal(N, p->W, parity);
-    std::vector<int> targets;
-    std::vector<int64_t> ls;
-    for (int64_t l = lo; l <= hi; ++l)
-      if ((l & 1) == parity) {
-        targets.push_back(red.n - 1 - (int)(l >> 1));
-        ls.push_back(l);
+struct PendingWin {
+  fst_plan_t p;
+  int64_t centre, Rw, lo, hi;
+  double *S;
+  bool done;
+};
+
+// The window vectors of a group of plans: both parities of every plan's window as one batch of
+// independent targets (bisection, inverse iteration one thread per target, expansion).
+static fst_status batched_window_vectors(std::vector<PendingWin *> &grp) {
+  if (grp.empty()) return FST_OK;
+  Runner *R0 = grp[0]->p->R;
+  Scoped sc(R0);
+  // concatenated reduced matrices and one descriptor per target
+  std::vector<double> dcat, ecat, e2cat;
+  std::vector<TargetDesc> td;
+  for (PendingWin *pw : grp) {
+    fst_plan_t p = pw->p;
+    for (int parity = 0; parity < 2; ++parity) {
+      Reduced red = reduced_tridiagonal(p->N, p->W, parity);
+      if (red.n == 0) continue;
+      double glo = 1e300, ghi = -1e300, tnorm = 0.0, emax2 = 0.0;
+      for (int i = 0; i < red.n; ++i) {
+        const double el = fabs(red.e[i]), er = (i + 1 < red.n) ? fabs(red.e[i + 1]) : 0.0;
+        glo = std::min(glo, red.d[i] - el - er);
+        ghi = std::max(ghi, red.d[i] + el + er);
+        tnorm = std::max(tnorm, fabs(red.d[i]) + el + er);
+        emax2 = std::max(emax2, red.e2[i]);
       }
-    if (targets.empty()) continue;
-    const int n = red.n, nt = (int)targets.size();
-    double glo = 1e300, ghi = -1e300, tnorm = 0.0, emax2 = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double el = fabs(red.e[i]), er = (i + 1 < n) ? fabs(red.e[i + 1]) : 0.0;
-      glo = std::min(glo, red.d[i] - el - er);
-      ghi = std::max(ghi, red.d[i] + el + er);
-      tnorm = std::max(tnorm, fabs(red.d[i]) + el + er);
-      emax2 = std::max(emax2, red.e2[i]);
+      const double pivmin = 2.2250738585072014e-308 * std::max(1.0, emax2);
+      const double widen = 2.220446049250313e-16 * tnorm * 4.0 + 4.0 * pivmin;
+      const int64_t off = (int64_t)dcat.size();
+      dcat.insert(dcat.end(), red.d.begin(), red.d.end());
+      ecat.insert(ecat.end(), red.e.begin(), red.e.end());
+      e2cat.insert(e2cat.end(), red.e2.begin(), red.e2.end());
+      for (int64_t l = pw->lo; l <= pw->hi; ++l) {
+        if ((l & 1) != parity) continue;
+        TargetDesc q{};
+        q.mat_off = off;
+        q.x_off = 0;
+        q.S = pw->S + (size_t)(l - pw->lo) * p->N;
+        q.N = p->N;
+        q.n = red.n;
+        q.target = red.n - 1 - (int)(l >> 1);
+        q.parity = parity;
+        q.glo = glo - widen;
+        q.ghi = ghi + widen;
+        q.pivmin = pivmin;
+        q.tol = 2.220446049250313e-16 * tnorm + pivmin;   // > 0 also for a zero matrix (N = 1)
+        td.push_back(q);
+      }
     }
-    const double pivmin = 2.2250738585072014e-308 * std::max(1.0, emax2);
-    const double widen = 2.220446049250313e-16 * tnorm * 4.0 + 4.0 * pivmin;
-    glo -= widen;
-    ghi += widen;
-    Scoped loc(R);
-    double *dd, *de, *de2, *theta, *x, *fd, *fdl, *fdu, *fdu2, *Sp;
-    int *dt, *flag;
-    uint8_t *piv;
-    TRY(loc.alloc(&dd, n));
-    TRY(loc.alloc(&de, n));
-    TRY(loc.alloc(&de2, n));
-    TRY(loc.alloc(&dt, nt));
-    TRY(loc.alloc(&theta, nt));
-    TRY(loc.alloc(&flag, 1));
-    TRY(R->h2d(dd, red.d.data(), n * sizeof(double)));
-    TRY(R->h2d(de, red.e.data(), n * sizeof(double)));
-    TRY(R->h2d(de2, red.e2.data(), n * sizeof(double)));
-    TRY(R->h2d(dt, targets.data(), nt * sizeof(int)));
-    TRY(R->zero(flag, sizeof(int)));
-    TRY(R->bisect(dd, de2, n, dt, nt, glo, ghi, pivmin, theta, flag));
-    int hflag = 0;
-    TRY(R->d2h(&hflag, flag, sizeof(int)));
-    if (hflag) return fail(FST_ENOCONVERGE, "bisection did not converge");
-    const size_t nn = (size_t)n * nt;
-    TRY(loc.alloc(&x, nn));
-    TRY(loc.alloc(&fd, nn));
-    TRY(loc.alloc(&fdl, nn));
-    TRY(loc.alloc(&fdu, nn));
-    TRY(loc.alloc(&fdu2, nn));
-    TRY(loc.alloc(&piv, nn));
-    TRY(R->invit(dd, de, n, theta, nt, 2.220446049250313e-16 * tnorm, 3, x, fd, fdl, fdu, fdu2, piv));
-    TRY(loc.alloc(&Sp, (size_t)nt * N));
-    TRY(R->finalize(x, n, nt, parity, N, Sp));
-    for (int k = 0; k < nt; ++k)
-      TRY(R->d2d(S + (size_t)(ls[k] - lo) * N, Sp + (size_t)k * N, (size_t)N * sizeof(double)));
   }
-  return window_eigenvalues(p, S, nwin, lam_host, spec_unit);
+  const int nt = (int)td.size();
+  double *dd, *de, *de2, *theta;
+  int *flag;
+  TargetDesc *dtd;
+  TRY(sc.alloc(&dd, dcat.size()));
+  TRY(sc.alloc(&de, ecat.size()));
+  TRY(sc.alloc(&de2, e2cat.size()));
+  TRY(sc.alloc(&theta, nt));
+  TRY(sc.alloc(&flag, 1));
+  TRY(sc.alloc(&dtd, nt));
+  TRY(R0->h2d(dd, dcat.data(), dcat.size() * sizeof(double)));
+  TRY(R0->h2d(de, ecat.data(), ecat.size() * sizeof(double)));
+  TRY(R0->h2d(de2, e2cat.data(), e2cat.size() * sizeof(double)));
+  TRY(R0->zero(flag, sizeof(int)));
+  TRY(R0->h2d(dtd, td.data(), td.size() * sizeof(TargetDesc)));
+  // few targets: multisection, one block each (fewer rounds; the GPU has room for the extra
+  // Sturm counts); many: plain bisection, one thread each (less arithmetic in all)
+  if (nt <= BISECT_MS_MAX_TARGETS) TRY(R0->bisect_ms_many(dtd, nt, dd, de2, theta, flag));
+  else TRY(R0->bisect_many(dtd, nt, dd, de2, theta, flag));
+  int hflag = 0;
+  TRY(R0->d2h(&hflag, flag, sizeof(int)));
+  if (hflag) return fail(FST_ENOCONVERGE, "bisection did not converge");
+  // inverse iteration and expansion in groups bounded by the factor storage
+  const int64_t budget = 192LL << 20;   // elements per factor array (41 bytes each in all)
+  for (int t0 = 0; t0 < nt;) {
+    int t1 = t0;
+    int64_t tot = 0;
+    while (t1 < nt && (tot + td[t1].n <= budget || t1 == t0)) {
+      td[t1].x_off = tot;
+      tot += td[t1].n;
+      ++t1;
+    }
+    Scoped g(R0);
+    double *x, *fd, *fdl, *fdu, *fdu2;
+    uint8_t *piv;
+    TargetDesc *gtd;
+    TRY(g.alloc(&x, tot));
+    TRY(g.alloc(&fd, tot));
+    TRY(g.alloc(&fdl, tot));
+    TRY(g.alloc(&fdu, tot));
+    TRY(g.alloc(&fdu2, tot));
+    TRY(g.alloc(&piv, tot));
+    TRY(g.alloc(&gtd, t1 - t0));
+    TRY(R0->h2d(gtd, td.data() + t0, (size_t)(t1 - t0) * sizeof(TargetDesc)));
+    TRY(R0->invit_many(gtd, t1 - t0, dd, de, theta + t0, x, fd, fdl, fdu, fdu2, piv));
+    TRY(R0->finalize_many(gtd, t1 - t0, x));
+    TRY(R0->sync());
+    t0 = t1;
+  }
+  return FST_OK;
+}
+
+static fst_status window_vectors(fst_plan_t p, int64_t lo, int64_t hi, double *S, double *lam_host,
+                                 const double *spec_unit) {
+  PendingWin pw{p, 0, 0, lo, hi, S, false};
+  std::vector<PendingWin *> grp{&pw};
+  TRY(batched_window_vectors(grp));
+  return window_eigenvalues(p, S, (int)(hi - lo + 1), lam_host, spec_unit);
 }
 
 static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
@@ -835,7 +885,7 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     fst_status s;
     if ((s = win.alloc(&Sw, (size_t)nwin * N)) != FST_OK) return bail(s);
     lamw.assign(nwin, 0.0);
-    if ((s = window_vectors(p, win, lo, hi, Sw, lamw.data(), spec_unit)) != FST_OK) return bail(s);
+    if ((s = window_vectors(p, lo, hi, Sw, lamw.data(), spec_unit)) != FST_OK) return bail(s);
     const bool lo_ok = (lo == 0) || !in_T(lamw[0], lo, K, eps, op, p->alpha);
     const bool hi_ok = (hi == N - 1) || !in_T(lamw[nwin - 1], hi, K, eps, op, p->alpha);
     if (lo_ok && hi_ok) {
@@ -1444,106 +1494,6 @@ fst_status fst_adi_shifts(int64_t N, int r, double *out) {
 // ===========================================================================
 namespace fst {
 
-struct PendingWin {
-  fst_plan_t p;
-  int64_t centre, Rw, lo, hi;
-  double *S;
-  bool done;
-};
-
-static fst_status batched_window_vectors(std::vector<PendingWin *> &grp) {
-  if (grp.empty()) return FST_OK;
-  Runner *R0 = grp[0]->p->R;
-  Scoped sc(R0);
-  // concatenated reduced matrices and one descriptor per target
-  std::vector<double> dcat, ecat, e2cat;
-  std::vector<TargetDesc> td;
-  for (PendingWin *pw : grp) {
-    fst_plan_t p = pw->p;
-    for (int parity = 0; parity < 2; ++parity) {
-      Reduced red = reduced_tridiagonal(p->N, p->W, parity);
-      if (red.n == 0) continue;
-      double glo = 1e300, ghi = -1e300, tnorm = 0.0, emax2 = 0.0;
-      for (int i = 0; i < red.n; ++i) {
-        const double el = fabs(red.e[i]), er = (i + 1 < red.n) ? fabs(red.e[i + 1]) : 0.0;
-        glo = std::min(glo, red.d[i] - el - er);
-        ghi = std::max(ghi, red.d[i] + el + er);
-        tnorm = std::max(tnorm, fabs(red.d[i]) + el + er);
-        emax2 = std::max(emax2, red.e2[i]);
-      }
-      const double pivmin = 2.2250738585072014e-308 * std::max(1.0, emax2);
-      const double widen = 2.220446049250313e-16 * tnorm * 4.0 + 4.0 * pivmin;
-      const int64_t off = (int64_t)dcat.size();
-      dcat.insert(dcat.end(), red.d.begin(), red.d.end());
-      ecat.insert(ecat.end(), red.e.begin(), red.e.end());
-      e2cat.insert(e2cat.end(), red.e2.begin(), red.e2.end());
-      for (int64_t l = pw->lo; l <= pw->hi; ++l) {
-        if ((l & 1) != parity) continue;
-        TargetDesc q{};
-        q.mat_off = off;
-        q.x_off = 0;
-        q.S = pw->S + (size_t)(l - pw->lo) * p->N;
-        q.N = p->N;
-        q.n = red.n;
-        q.target = red.n - 1 - (int)(l >> 1);
-        q.parity = parity;
-        q.glo = glo - widen;
-        q.ghi = ghi + widen;
-        q.pivmin = pivmin;
-        q.tol = 2.220446049250313e-16 * tnorm;
-        td.push_back(q);
-      }
-    }
-  }
-  const int nt = (int)td.size();
-  double *dd, *de, *de2, *theta;
-  int *flag;
-  TargetDesc *dtd;
-  TRY(sc.alloc(&dd, dcat.size()));
-  TRY(sc.alloc(&de, ecat.size()));
-  TRY(sc.alloc(&de2, e2cat.size()));
-  TRY(sc.alloc(&theta, nt));
-  TRY(sc.alloc(&flag, 1));
-  TRY(sc.alloc(&dtd, nt));
-  TRY(R0->h2d(dd, dcat.data(), dcat.size() * sizeof(double)));
-  TRY(R0->h2d(de, ecat.data(), ecat.size() * sizeof(double)));
-  TRY(R0->h2d(de2, e2cat.data(), e2cat.size() * sizeof(double)));
-  TRY(R0->zero(flag, sizeof(int)));
-  TRY(R0->h2d(dtd, td.data(), td.size() * sizeof(TargetDesc)));
-  TRY(R0->bisect_many(dtd, nt, dd, de2, theta, flag));
-  int hflag = 0;
-  TRY(R0->d2h(&hflag, flag, sizeof(int)));
-  if (hflag) return fail(FST_ENOCONVERGE, "bisection did not converge");
-  // inverse iteration and expansion in groups bounded by the factor storage
-  const int64_t budget = 48LL << 20;   // elements per factor array
-  for (int t0 = 0; t0 < nt;) {
-    int t1 = t0;
-    int64_t tot = 0;
-    while (t1 < nt && (tot + td[t1].n <= budget || t1 == t0)) {
-      td[t1].x_off = tot;
-      tot += td[t1].n;
-      ++t1;
-    }
-    Scoped g(R0);
-    double *x, *fd, *fdl, *fdu, *fdu2;
-    uint8_t *piv;
-    TargetDesc *gtd;
-    TRY(g.alloc(&x, tot));
-    TRY(g.alloc(&fd, tot));
-    TRY(g.alloc(&fdl, tot));
-    TRY(g.alloc(&fdu, tot));
-    TRY(g.alloc(&fdu2, tot));
-    TRY(g.alloc(&piv, tot));
-    TRY(g.alloc(&gtd, t1 - t0));
-    TRY(R0->h2d(gtd, td.data() + t0, (size_t)(t1 - t0) * sizeof(TargetDesc)));
-    TRY(R0->invit_many(gtd, t1 - t0, dd, de, theta + t0, x, fd, fdl, fdu, fdu2, piv));
-    TRY(R0->finalize_many(gtd, t1 - t0, x));
-    TRY(R0->sync());
-    t0 = t1;
-  }
-  return FST_OK;
-}
-
 fst_status build_plans_many(Runner *(*mk)(), void *stream, int64_t count, const int64_t *N, const double *W,
                             const int64_t *K, const double *eps, fst_plan_t *out) {
   if (!out || count < 0 || (count > 0 && (!N || !W || !eps))) return fail(FST_EINVAL, "bad arguments");
@@ -1575,12 +1525,13 @@ fst_status build_plans_many(Runner *(*mk)(), void *stream, int64_t count, const 
     for (auto &q : pw)
       if (!q.done) pend.push_back(&q);
     if (pend.empty()) break;
-    // groups bounded by the host/device size of the window vectors
+    // groups bounded by the device size of the window vectors (2^31 doubles, 16 GiB): large
+    // enough that the batched bisection has targets for every SM
     size_t gi = 0;
     while (gi < pend.size()) {
       std::vector<PendingWin *> grp;
       int64_t elems = 0;
-      while (gi < pend.size() && (grp.empty() || elems < (256LL << 20))) {
+      while (gi < pend.size() && (grp.empty() || elems < (2048LL << 20))) {
         PendingWin *q = pend[gi++];
         fst_plan_t p = q->p;
         q->lo = std::max<int64_t>(0, q->centre - q->Rw);

@@ -107,13 +107,10 @@ struct Runner {
   virtual fst_status zadd(const ConvArgs<float> &a) { return FST_EUNSUPPORTED; }
 
   // plan kernels (all pointers in runner memory)
-  virtual fst_status bisect(const double *d, const double *e2, int n, const int *targets, int nt, double glo,
-                            double ghi, double pivmin, double *out, int *flag) = 0;
-  virtual fst_status invit(const double *d, const double *e, int n, const double *sigma, int nt, double tol,
-                           int iters, double *x, double *fd, double *fdl, double *fdu, double *fdu2,
-                           uint8_t *piv) = 0;
-  virtual fst_status finalize(const double *x, int n, int nt, int parity, int64_t N, double *S) = 0;
-  // batched eigen-targets of many plans (descriptors and data in runner memory)
+  // batched eigen-targets of one or many plans (descriptors and data in runner memory):
+  // multisection (a block of BISECT_THREADS per target) or plain bisection (a thread per target)
+  virtual fst_status bisect_ms_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat,
+                                    double *theta, int *flag) = 0;
   virtual fst_status bisect_many(const TargetDesc *td, int nt, const double *dcat, const double *e2cat,
                                  double *theta, int *flag) = 0;
   virtual fst_status invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat,

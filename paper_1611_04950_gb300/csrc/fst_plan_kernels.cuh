@@ -17,23 +17,55 @@
 #pragma once
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 #include "fst_fft.cuh"
 
 namespace fst {
 
 constexpr int BISECT_THREADS = 64;
+constexpr int BISECT_MS_MAX_TARGETS = 512;   // batches up to this many targets use multisection
 constexpr int BISECT_MAX_ROUNDS = 24;
 
-// number of eigenvalues of the reduced matrix smaller than x (negative LDL^T pivots)
+// biased exponent field of a double (0 for zeros and subnormals)
+FST_HD int dexp_field(double v) {
+#ifdef __CUDA_ARCH__
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+#else
+  uint64_t u;
+  memcpy(&u, &v, 8);
+  return (int)((u >> 52) & 0x7ff);
+#endif
+}
+
+// Number of eigenvalues of the reduced matrix smaller than x: the sign changes of the Sturm
+// sequence of leading principal minors p_i = det(T_i - x I), p_i = (d_i - x) p_{i-1} -
+// e_i^2 p_{i-2} (p_{-1} = 1), which equal the negative pivots q_i = p_i / p_{i-1} of
+// T - x I = L D L^T.  The recurrence needs no division (the serial chain is one FMA per step);
+// every 4 steps the pair (p_i, p_{i-1}) is rescaled by an exact power of two when both are
+// beyond 2^(+-400) (a step grows them by at most about 2^87 for N <= 2^23), and an exact zero
+// p_i is replaced by -pivmin p_{i-1} (the pivot -pivmin of the LDL^T form).
 FST_HD int sturm_count(const double *d, const double *e2, int n, double x, double pivmin) {
-  int c = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  c += (q < 0.0);
+  double pm = 1.0, p = ldg(d) - x;
+  if (p == 0.0) p = -pivmin;
+  int c = (p < 0.0);
   for (int i = 1; i < n; ++i) {
-    q = (ldg(d + i) - x) - ldg(e2 + i) / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += (q < 0.0);
+    const double t = ldg(e2 + i) * pm;
+    double pn = fma(ldg(d + i) - x, p, -t);
+    if (pn == 0.0) pn = -pivmin * p;
+    c += ((pn < 0.0) != (p < 0.0));
+    pm = p;
+    p = pn;
+    if ((i & 3) == 0) {
+      const int ex = dexp_field(p), exm = dexp_field(pm);
+      const int mx = ex > exm ? ex : exm;
+      if (mx > 1023 + 400) {
+        p *= 0x1p-512;
+        pm *= 0x1p-512;
+      } else if (mx < 1023 - 400) {
+        p *= 0x1p512;
+        pm *= 0x1p512;
+      }
+    }
   }
   return c;
 }
@@ -118,78 +150,162 @@ struct TargetDesc {
 // classical tridiagonal elimination; row interchanges create a second
 // superdiagonal), zero pivots lifted to tol, then `iters` solves with the same
 // factors, each followed by scaling to max-norm 1.  Vector t of nt: element i at
-// [i * nt + t] in x and in the factor arrays (interleaved: coalesced across t).
+// [i * nt + t] in x and in the factor arrays.  fd holds the reciprocals of the
+// (lifted) U diagonal, so the back substitution multiplies.
+//
+// Each phase is a serial chain over i.  The entries a step updates travel to the next
+// step in registers (cd, cu: U diagonal and super-diagonal at i; cur: x[i]; x1, x2:
+// x[i+1], x[i+2]), and the inputs of the next INVIT_B steps are loaded while the current
+// ones are processed (the loads never touch an entry the current block writes), so the
+// chain waits on arithmetic, not on memory.
+constexpr int INVIT_B = 8;
 FST_HD void invit_body(const double *d, const double *e, int n, double sigma, double tol, int iters, int t, int nt,
                        double *x, double *fd, double *fdl, double *fdu, double *fdu2, uint8_t *piv) {
 #define AT(a, i) a[(int64_t)(i) * nt + t]
-  // The elimination and both sweeps carry the entries they update from one step to the next in
-  // registers (cd, cu: the current U diagonal and super-diagonal at i; cur: x[i]; x1, x2: x[i+1],
-  // x[i+2]), so each step reads only inputs and the serial chain never waits on a memory round
-  // trip.  Same operations, same order as the textbook in-place form.
+  constexpr int B = INVIT_B;
   auto lift = [&](double p) { return (fabs(p) < tol) ? ((p < 0.0) ? -tol : tol) : p; };
-  // factor: fd = U diagonal (zero pivots lifted to tol), fdu / fdu2 = U super-diagonals,
-  // fdl = multipliers
-  double cd = ldg(d) - sigma;
-  double cu = (n > 1) ? ldg(e + 1) : 0.0;
-  for (int i = 0; i + 1 < n; ++i) {
-    const double li = ldg(e + i + 1);
-    const double nd = ldg(d + i + 1) - sigma;
-    const double nu = (i + 2 < n) ? ldg(e + i + 2) : 0.0;
-    if (fabs(cd) >= fabs(li)) {
-      const double f = (cd != 0.0) ? li / cd : 0.0;
-      AT(fdl, i) = f;
-      AT(fd, i) = lift(cd);
-      AT(fdu, i) = cu;
-      AT(fdu2, i) = 0.0;
-      AT(piv, i) = 0;
-      cd = nd - f * cu;
-      cu = nu;
-    } else {
-      const double f = cd / li;
-      AT(fdl, i) = f;
-      AT(fd, i) = lift(li);
-      AT(fdu, i) = nd;
-      AT(fdu2, i) = (i + 2 < n) ? nu : 0.0;
-      AT(piv, i) = 1;
-      cd = cu - f * nd;
-      cu = (i + 2 < n) ? -f * nu : 0.0;
+  // ---- factor: steps i = 0 .. n-2 read e[i+1], d[i+1], e[i+2]
+  {
+    double cd = ldg(d) - sigma;
+    double cu = (n > 1) ? ldg(e + 1) : 0.0;
+    double E[B + 1], D[B];
+    auto load = [&](int i0, double *Ev, double *Dv) {
+#pragma unroll
+      for (int k = 0; k <= B; ++k) Ev[k] = (i0 + 1 + k < n) ? ldg(e + i0 + 1 + k) : 0.0;
+#pragma unroll
+      for (int k = 0; k < B; ++k) Dv[k] = (i0 + 1 + k < n) ? ldg(d + i0 + 1 + k) : 0.0;
+    };
+    load(0, E, D);
+    for (int i0 = 0; i0 + 1 < n; i0 += B) {
+      double En[B + 1], Dn[B];
+      load(i0 + B, En, Dn);
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        const int i = i0 + k;
+        if (i + 1 < n) {
+          const double li = E[k], nd = D[k] - sigma, nu = (i + 2 < n) ? E[k + 1] : 0.0;
+          if (fabs(cd) >= fabs(li)) {
+            const double f = (cd != 0.0) ? li / cd : 0.0;
+            AT(fdl, i) = f;
+            AT(fd, i) = 1.0 / lift(cd);
+            AT(fdu, i) = cu;
+            AT(fdu2, i) = 0.0;
+            AT(piv, i) = 0;
+            cd = nd - f * cu;
+            cu = nu;
+          } else {
+            const double f = cd / li;
+            AT(fdl, i) = f;
+            AT(fd, i) = 1.0 / lift(li);
+            AT(fdu, i) = nd;
+            AT(fdu2, i) = nu;
+            AT(piv, i) = 1;
+            cd = cu - f * nd;
+            cu = -f * nu;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k <= B; ++k) E[k] = En[k];
+#pragma unroll
+      for (int k = 0; k < B; ++k) D[k] = Dn[k];
     }
+    AT(fd, n - 1) = 1.0 / lift(cd);
+    AT(fdu, n - 1) = 0.0;
+    AT(fdl, n - 1) = 0.0;
+    AT(fdu2, n - 1) = 0.0;
+    AT(piv, n - 1) = 0;
   }
-  AT(fd, n - 1) = lift(cd);
-  AT(fdu, n - 1) = 0.0;
-  AT(fdl, n - 1) = 0.0;
-  AT(fdu2, n - 1) = 0.0;
-  AT(piv, n - 1) = 0;
   // start vector: deterministic, no structure shared with any eigenvector
   for (int i = 0; i < n; ++i) {
     const double g = (double)i * 0.6180339887498949;
     AT(x, i) = 0.5 + (g - floor(g));
   }
   for (int it = 0; it < iters; ++it) {
-    // L solve with the row interchanges
-    double cur = AT(x, 0);
-    for (int i = 0; i + 1 < n; ++i) {
-      const double nx = AT(x, i + 1), l = AT(fdl, i);
-      if (AT(piv, i) == 0) {
-        AT(x, i) = cur;
-        cur = nx - l * cur;
-      } else {
-        AT(x, i) = nx;
-        cur = cur - l * nx;
+    // ---- L solve with the row interchanges: step i reads x[i+1] (not yet written), fdl[i], piv[i]
+    {
+      double cur = AT(x, 0);
+      double X[B], L[B];
+      unsigned PV;
+      auto load = [&](int i0, double *Xv, double *Lv, unsigned &pv) {
+        pv = 0u;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const bool ok = i0 + k + 1 < n;
+          Xv[k] = ok ? AT(x, i0 + k + 1) : 0.0;
+          Lv[k] = ok ? AT(fdl, i0 + k) : 0.0;
+          pv |= (ok && AT(piv, i0 + k)) ? (1u << k) : 0u;
+        }
+      };
+      load(0, X, L, PV);
+      for (int i0 = 0; i0 + 1 < n; i0 += B) {
+        double Xn[B], Ln[B];
+        unsigned PVn;
+        load(i0 + B, Xn, Ln, PVn);
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int i = i0 + k;
+          if (i + 1 < n) {
+            if (((PV >> k) & 1u) == 0u) {
+              AT(x, i) = cur;
+              cur = X[k] - L[k] * cur;
+            } else {
+              AT(x, i) = X[k];
+              cur = cur - L[k] * X[k];
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          X[k] = Xn[k];
+          L[k] = Ln[k];
+        }
+        PV = PVn;
       }
+      AT(x, n - 1) = cur;
     }
-    AT(x, n - 1) = cur;
-    // U solve, max-norm
-    double mx = 0.0, x1 = 0.0, x2 = 0.0;
-    for (int i = n - 1; i >= 0; --i) {
-      double v = AT(x, i);
-      if (i + 1 < n) v -= AT(fdu, i) * x1;
-      if (i + 2 < n) v -= AT(fdu2, i) * x2;
-      v /= AT(fd, i);
-      AT(x, i) = v;
-      mx = fmax(mx, fabs(v));
-      x2 = x1;
-      x1 = v;
+    // ---- U solve (descending), max-norm: step i reads x[i], fdu[i], fdu2[i], fd[i]
+    double mx = 0.0;
+    {
+      double x1 = 0.0, x2 = 0.0;
+      double X[B], U1[B], U2[B], R[B];
+      auto load = [&](int i1, double *Xv, double *U1v, double *U2v, double *Rv) {
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int i = i1 - k;
+          const bool ok = i >= 0;
+          Xv[k] = ok ? AT(x, i) : 0.0;
+          U1v[k] = ok ? AT(fdu, i) : 0.0;
+          U2v[k] = ok ? AT(fdu2, i) : 0.0;
+          Rv[k] = ok ? AT(fd, i) : 0.0;
+        }
+      };
+      load(n - 1, X, U1, U2, R);
+      for (int i1 = n - 1; i1 >= 0; i1 -= B) {
+        double Xn[B], U1n[B], U2n[B], Rn[B];
+        load(i1 - B, Xn, U1n, U2n, Rn);
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int i = i1 - k;
+          if (i >= 0) {
+            double v = X[k];
+            if (i + 1 < n) v -= U1[k] * x1;
+            if (i + 2 < n) v -= U2[k] * x2;
+            v *= R[k];
+            AT(x, i) = v;
+            mx = fmax(mx, fabs(v));
+            x2 = x1;
+            x1 = v;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          X[k] = Xn[k];
+          U1[k] = U1n[k];
+          U2[k] = U2n[k];
+          R[k] = Rn[k];
+        }
+      }
     }
     const double s = (mx > 0.0) ? 1.0 / mx : 1.0;
     for (int i = 0; i < n; ++i) AT(x, i) = AT(x, i) * s;
