@@ -447,6 +447,7 @@ static fst_status set_attrs() {
   CU(cudaFuncSetAttribute(k_zadd, cudaFuncAttributeMaxDynamicSharedMemorySize, za_smem(64, 1)), "attr");
   CU(cudaFuncSetAttribute(k_fastB8192, cudaFuncAttributeMaxDynamicSharedMemorySize, fastb8192_smem()), "attr");
   CU(cudaFuncSetAttribute(k_fastB4096_2s, cudaFuncAttributeMaxDynamicSharedMemorySize, fastb2s_smem()), "attr");
+  CU(cudaFuncSetAttribute(k_rcorr_part, cudaFuncAttributeMaxDynamicSharedMemorySize, rcorr_smem()), "attr");
   CU(cudaFuncSetAttribute(k_colA<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(2)), "attr");
   CU(cudaFuncSetAttribute(k_colA<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(4)), "attr");
   CU(cudaFuncSetAttribute(k_colA<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_smem_bytes(8)), "attr");
@@ -908,7 +909,8 @@ struct DevRunner : Runner {
   fst_status rcorr(const RSig *sigs, int nsig, const RItem *items, int nitems, int cplx, float *part,
                    float *acoef) override {
     if (nitems <= 0) return FST_OK;
-    PROF("k_rcorr_part", nitems, (k_rcorr_part<<<(unsigned)nitems, 256, 0, cur>>>(sigs, items, cplx, part)));
+    TRY(set_attrs());
+    PROF("k_rcorr_part", nitems, (k_rcorr_part<<<(unsigned)nitems, 256, rcorr_smem(), cur>>>(sigs, items, cplx, part)));
     LAUNCHED("k_rcorr_part");
     PROF("k_rcorr_reduce", nsig, (k_rcorr_reduce<<<(unsigned)nsig, 128, 0, cur>>>(sigs, part, acoef)));
     LAUNCHED("k_rcorr_reduce");

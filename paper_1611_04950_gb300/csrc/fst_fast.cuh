@@ -1166,43 +1166,27 @@ __global__ void __launch_bounds__(CC_THREADS) k_corr_cc(const ConvArgs<float> a)
 //   k_rzadd        item: out(n) and out(N-1-n) += ... for the chunk's n (thread per n)
 // acoef: [signal][2][RC_RMAX]
 // ---------------------------------------------------------------------------
-// one folded sample of k_rcorr_part: the thread's float4 of S_T row n against y(n) +- y(N-1-n),
-// the sign by the parity bits `odd` of its four columns
-__device__ __forceinline__ void rcorr_one(const RSig &q, int cplx, const float4 *S4, int tpr, int jq, unsigned odd,
-                                          int64_t n, float *ar, float *ai) {
-  const int64_t m = q.N - 1 - n;
-  float yr, yi = 0.f, mr = 0.f, mi = 0.f;
-  if (cplx) {
-    const float2 v = reinterpret_cast<const float2 *>(q.y)[n];
-    yr = v.x;
-    yi = v.y;
-    if (m != n) {
-      const float2 w = reinterpret_cast<const float2 *>(q.y)[m];
-      mr = w.x;
-      mi = w.y;
-    }
-  } else {
-    yr = q.y[n];
-    if (m != n) mr = q.y[m];
-  }
-  const float4 s4 = __ldg(S4 + n * tpr + jq);
-  const float pr = yr + mr, dr = yr - mr, pi = yi + mi, di = yi - mi;
-  ar[0] = fmaf(s4.x, (odd & 1u) ? dr : pr, ar[0]);
-  ar[1] = fmaf(s4.y, (odd & 2u) ? dr : pr, ar[1]);
-  ar[2] = fmaf(s4.z, (odd & 4u) ? dr : pr, ar[2]);
-  ar[3] = fmaf(s4.w, (odd & 8u) ? dr : pr, ar[3]);
-  ai[0] = fmaf(s4.x, (odd & 1u) ? di : pi, ai[0]);
-  ai[1] = fmaf(s4.y, (odd & 2u) ? di : pi, ai[1]);
-  ai[2] = fmaf(s4.z, (odd & 4u) ? di : pi, ai[2]);
-  ai[3] = fmaf(s4.w, (odd & 8u) ? di : pi, ai[3]);
+// The chunk's S_T rows are one contiguous block ([n][rpad]).  The block streams it through a
+// ring of RC_NST shared-memory tiles of rpr * RC_U rows (rpr = 256 / tpr rows per round, tpr =
+// rpad / 4 threads per row) with 16-byte cp.async copies, RC_NST - 1 tiles in flight, together
+// with each row's y(n) and y(N-1-n).  Thread t takes the float4 jq = t mod tpr of rows t / tpr,
+// t / tpr + rpr, ... (in increasing order), folds y(n) +- y(N-1-n) by the parity of each of its
+// four columns and accumulates; fixed-order sums at the end.
+constexpr int RC_U = 4, RC_NST = 3;
+constexpr int RC_S_F = 256 * RC_U * 4;            // S floats per tile (1024 float4 at most)
+constexpr int RC_STAGE_F = RC_S_F + 4 * 512;      // + y: up to 512 rows x (re, im) x (n, N-1-n)
+constexpr int rcorr_smem() { return RC_NST * RC_STAGE_F * 4; }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
-
-// The chunk's S_T rows are one contiguous block ([n][rpad]); the block streams it in 16-byte
-// pieces: thread t takes the float4 jq = t mod tpr (tpr = rpad/4 threads per row) of rows
-// t / tpr, t / tpr + rpr, ... (rpr = 256 / tpr rows per round, four rounds in flight), folding
-// y(n) +- y(N-1-n) by the parity of each of its four columns.  Fixed-order sums at the end.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_ring() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(RC_NST - 1) : "memory");
+}
 __global__ void __launch_bounds__(256) k_rcorr_part(const RSig *sigs, const RItem *items, int cplx, float *part) {
-  __shared__ float red[2048];   // [row slot][comp][j]: rpr * 2 * rpad <= 2048 floats
+  extern __shared__ __align__(16) float rsm[];
   const RItem it = items[blockIdx.x];
   const RSig q = sigs[it.sig];
   const int tpr = q.rpad / 4, rpr = 256 / tpr;
@@ -1210,22 +1194,87 @@ __global__ void __launch_bounds__(256) k_rcorr_part(const RSig *sigs, const RIte
   const bool active = slot < rpr;
   const int64_t H = (q.N + 1) / 2;
   const int64_t n0 = (int64_t)it.chunk * CORR_BLOCK;
-  const int64_t nend = (H - n0 < CORR_BLOCK) ? H : n0 + CORR_BLOCK;
+  const int rows_total = (int)((H - n0 < CORR_BLOCK) ? H - n0 : CORR_BLOCK);
+  const int trows = rpr * RC_U;
+  const int ntiles = (rows_total + trows - 1) / trows;
   const int jb = (4 * jq) & (RC_RMAX - 1);
   // 4 j never straddle a word (jb % 4 == 0); the word is read from the descriptor in global
   // memory (a runtime index into the register copy would put it in local memory)
   const unsigned odd = (__ldg(&sigs[it.sig].odd[jb >> 5]) >> (jb & 31)) & 15u;
-  float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-  if (active) {
-    const float4 *S4 = reinterpret_cast<const float4 *>(q.ST);
-    int64_t n = n0 + slot;
-    for (; n + 3 * rpr < nend; n += 4 * rpr) {
-      rcorr_one(q, cplx, S4, tpr, jq, odd, n, ar, ai);
-      rcorr_one(q, cplx, S4, tpr, jq, odd, n + rpr, ar, ai);
-      rcorr_one(q, cplx, S4, tpr, jq, odd, n + 2 * rpr, ar, ai);
-      rcorr_one(q, cplx, S4, tpr, jq, odd, n + 3 * rpr, ar, ai);
+  const float4 *S4 = reinterpret_cast<const float4 *>(q.ST);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(rsm);
+  auto issue = [&](int tile) {
+    const uint32_t st = sbase + (uint32_t)((tile % RC_NST) * RC_STAGE_F * 4);
+    const int r0 = tile * trows;
+    const int rows = (rows_total - r0 < trows) ? rows_total - r0 : trows;
+    const float4 *src = S4 + (n0 + r0) * tpr;
+    for (int e = threadIdx.x; e < rows * tpr; e += 256) cp_async16(st + (uint32_t)(e * 16), src + e, 16);
+    const uint32_t yv = st + (uint32_t)(RC_S_F * 4);
+    for (int r = threadIdx.x; r < rows; r += 256) {
+      const int64_t n = n0 + r0 + r, m = q.N - 1 - n;
+      if (cplx) {
+        cp_async8(yv + (uint32_t)(r * 16), q.y + 2 * n);
+        cp_async8(yv + (uint32_t)(r * 16 + 8), q.y + 2 * m);
+      } else {
+        cp_async4(yv + (uint32_t)(r * 8), q.y + n);
+        cp_async4(yv + (uint32_t)(r * 8 + 4), q.y + m);
+      }
     }
-    for (; n < nend; n += rpr) rcorr_one(q, cplx, S4, tpr, jq, odd, n, ar, ai);
+  };
+#pragma unroll
+  for (int t = 0; t < RC_NST - 1; ++t) {
+    if (t < ntiles) issue(t);
+    cp_async_commit();
+  }
+  float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int t = 0; t < ntiles; ++t) {
+    if (t + RC_NST - 1 < ntiles) issue(t + RC_NST - 1);
+    cp_async_commit();
+    cp_async_wait_ring();   // this thread's copies of tile t have landed
+    __syncthreads();        // and everyone else's
+    if (active) {
+      const float *st = rsm + (t % RC_NST) * RC_STAGE_F;
+      const float *yv = st + RC_S_F;
+      const int r0 = t * trows;
+      const int rows = (rows_total - r0 < trows) ? rows_total - r0 : trows;
+#pragma unroll
+      for (int u = 0; u < RC_U; ++u) {
+        const int r = slot + rpr * u;
+        if (r < rows) {
+          const float4 s4 = reinterpret_cast<const float4 *>(st)[r * tpr + jq];
+          const int64_t n = n0 + r0 + r, m = q.N - 1 - n;
+          float yr, yi = 0.f, mr = 0.f, mi = 0.f;
+          if (cplx) {
+            const float4 v = reinterpret_cast<const float4 *>(yv)[r];
+            yr = v.x;
+            yi = v.y;
+            if (m != n) {
+              mr = v.z;
+              mi = v.w;
+            }
+          } else {
+            const float2 v = reinterpret_cast<const float2 *>(yv)[r];
+            yr = v.x;
+            if (m != n) mr = v.y;
+          }
+          const float pr = yr + mr, dr = yr - mr, pi = yi + mi, di = yi - mi;
+          ar[0] = fmaf(s4.x, (odd & 1u) ? dr : pr, ar[0]);
+          ar[1] = fmaf(s4.y, (odd & 2u) ? dr : pr, ar[1]);
+          ar[2] = fmaf(s4.z, (odd & 4u) ? dr : pr, ar[2]);
+          ar[3] = fmaf(s4.w, (odd & 8u) ? dr : pr, ar[3]);
+          ai[0] = fmaf(s4.x, (odd & 1u) ? di : pi, ai[0]);
+          ai[1] = fmaf(s4.y, (odd & 2u) ? di : pi, ai[1]);
+          ai[2] = fmaf(s4.z, (odd & 4u) ? di : pi, ai[2]);
+          ai[3] = fmaf(s4.w, (odd & 8u) ? di : pi, ai[3]);
+        }
+      }
+    }
+    __syncthreads();        // tile t's slot is refilled by tile t + RC_NST at the next issue
+  }
+  cp_async_wait0();
+  // the ring is free: [row slot][comp][j], rpr * 2 * rpad <= 2048 floats
+  float *red = rsm;
+  if (active) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       red[(slot * 2 + 0) * q.rpad + 4 * jq + u] = ar[u];
