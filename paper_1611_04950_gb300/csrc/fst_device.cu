@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -83,6 +84,11 @@ __global__ void __launch_bounds__(1024) k_small_ragged(const RaggedDesc<T> *d, c
   T *red = reinterpret_cast<T *>(smem + padded_size(L) * sizeof(c2<T>));
   T *coef = red + ((blockDim.x + 31) / 32) * 128;
   const RaggedDesc<T> q = d[blockIdx.x];
+  if (q.y2) {
+    DevEx<T> ex;
+    small_pair_body<T>(ex, base, q, buf, red, coef);
+    return;
+  }
   ConvArgs<T> a = base;
   a.y = q.y;
   a.out = q.out;
@@ -1275,7 +1281,10 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
     default: return fail(FST_EINVAL, "unknown dtype");
   }
   const size_t sig_bytes = esz * (size_t)p->N;
-  int64_t per = std::max<int64_t>(2, (int64_t)((64u << 20) / sig_bytes));
+  // chunk of the pipeline: FST_HOST_CHUNK_MB (default 64) MiB of signals
+  const char *env = getenv("FST_HOST_CHUNK_MB");
+  const int64_t chunk_mb = std::max<int64_t>(1, env ? atoll(env) : 64);
+  int64_t per = std::max<int64_t>(2, (int64_t)(((size_t)chunk_mb << 20) / sig_bytes));
   per = (per / 2) * 2;
   per = std::min<int64_t>(per, ((batch + 1) / 2) * 2);
   const size_t slot = (size_t)per * sig_bytes;

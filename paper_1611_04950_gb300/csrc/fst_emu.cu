@@ -101,6 +101,11 @@ struct EmuRunner : Runner {
     T *red = reinterpret_cast<T *>(smem.data() + padded_size(Lsz) * sizeof(c2<T>));
     T *coef = red + ((L.nthr_small + 31) / 32) * 128;
     for (int i = 0; i < count; ++i) {
+      if (d[i].y2) {
+        HostEx<KState<T>> ex(L.nthr_small);
+        small_pair_body<T>(ex, base, d[i], buf, red, coef);
+        continue;
+      }
       ConvArgs<T> a = base;
       a.y = d[i].y;
       a.out = d[i].out;

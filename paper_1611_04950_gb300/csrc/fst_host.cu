@@ -1779,7 +1779,7 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
     fst_plan_t p = plans[i];
     const Layout &L = dbl ? p->lay64 : p->lay32;
     if (L.small) {
-      RaggedDesc<T> d;
+      RaggedDesc<T> d{};
       d.y = (const T *)y[i];
       d.out = (T *)out[i];
       d.spec = (const T *)(dbl ? (const void *)p->spec64 : (const void *)p->spec32);
@@ -1792,6 +1792,29 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
       maxr[p->log2M] = std::max(maxr[p->log2M], (int)p->rpad);
     } else {
       others.push_back(i);
+    }
+  }
+  // real signals share a CTA two at a time (the second as the imaginary part, its own spectrum
+  // and correction)
+  if (!cplx) {
+    for (auto &b : buckets) {
+      std::vector<RaggedDesc<T>> pb;
+      for (size_t k = 0; k < b.size(); k += 2) {
+        RaggedDesc<T> d = b[k];
+        if (k + 1 < b.size()) {
+          const RaggedDesc<T> &e = b[k + 1];
+          d.y2 = e.y;
+          d.out2 = e.out;
+          d.spec2 = e.spec;
+          d.ST2 = e.ST;
+          d.D2 = e.D;
+          d.N2 = e.N;
+          d.r2 = e.r;
+          d.rpad2 = e.rpad;
+        }
+        pb.push_back(d);
+      }
+      b.swap(pb);
     }
   }
   for (int lg = 0; lg < 32; ++lg) {

@@ -338,6 +338,25 @@ def test_emulated_plan_many_and_ragged_projection():
             assert np.linalg.norm(o - O.fast_project(op, y)) <= tol * np.linalg.norm(y)
 
 
+def test_emulated_ragged_small_signals_share_ctas():
+    # real single-CTA signals of one FFT length go two to a CTA (the second as the imaginary
+    # part, its own spectrum and correction); an odd count leaves one alone; ranks differ
+    params = [(1100, 0.05, 1e-3), (1500, 0.2, 1e-8), (2048, 0.1, 1e-6), (1025, 0.3, 1e-4), (1800, 0.02, 1e-6)]
+    ps = F.PlanSet(params, emulate=True)
+    rng = np.random.default_rng(4)
+    ys = [rng.standard_normal(N) for (N, W, e) in params]
+    plans = [O.make_plan(N, W, None, e) for (N, W, e) in params]
+    assert len({ps.info(i)["r"] for i in range(len(params))}) > 1
+    for dt, tol in ((np.float64, 1e-12), (np.float32, 1e-6)):
+        outs = ps.project([y.astype(dt) for y in ys])
+        for y, o, op in zip(ys, outs, plans):
+            assert np.linalg.norm(o - O.fast_project(op, y)) <= tol * np.linalg.norm(y)
+        io = [y.astype(dt) for y in ys]
+        ps.project(io, io)                      # in place
+        for a, b in zip(outs, io):
+            assert np.array_equal(a, b)
+
+
 def test_plan_many_rejects_bad_arguments():
     with pytest.raises(F.FSTError):
         F.fst_plan_many([100, 0], [0.1, 0.1], [1e-6, 1e-6], emulate=True)
