@@ -84,11 +84,6 @@ __global__ void __launch_bounds__(1024) k_small_ragged(const RaggedDesc<T> *d, c
   T *red = reinterpret_cast<T *>(smem + padded_size(L) * sizeof(c2<T>));
   T *coef = red + ((blockDim.x + 31) / 32) * 128;
   const RaggedDesc<T> q = d[blockIdx.x];
-  if (q.y2) {
-    DevEx<T> ex;
-    small_pair_body<T>(ex, base, q, buf, red, coef);
-    return;
-  }
   ConvArgs<T> a = base;
   a.y = q.y;
   a.out = q.out;
@@ -140,7 +135,7 @@ __global__ void k_bisect_ms_many(const TargetDesc *td, const double *dcat, const
   __shared__ BisectShared sh;
   DevExPlan ex;
   const TargetDesc q = td[blockIdx.x];
-  bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + blockIdx.x,
+  bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, q.tol, theta + blockIdx.x,
               flag, &sh);
 }
 
@@ -149,7 +144,7 @@ __global__ void k_bisect_many(const TargetDesc *td, int nt, const double *dcat, 
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const TargetDesc q = td[t];
-  bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag);
+  bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, q.tol, theta + t, flag);
 }
 __global__ void k_invit_many(const TargetDesc *td, int nt, const double *dcat, const double *ecat,
                              const double *theta, double *x, double *fd, double *fdl, double *fdu, double *fdu2,

@@ -101,11 +101,6 @@ struct EmuRunner : Runner {
     T *red = reinterpret_cast<T *>(smem.data() + padded_size(Lsz) * sizeof(c2<T>));
     T *coef = red + ((L.nthr_small + 31) / 32) * 128;
     for (int i = 0; i < count; ++i) {
-      if (d[i].y2) {
-        HostEx<KState<T>> ex(L.nthr_small);
-        small_pair_body<T>(ex, base, d[i], buf, red, coef);
-        continue;
-      }
       ConvArgs<T> a = base;
       a.y = d[i].y;
       a.out = d[i].out;
@@ -142,7 +137,7 @@ struct EmuRunner : Runner {
       const TargetDesc &q = td[t];
       BisectShared sh;
       HostEx<NoStateH> ex(BISECT_THREADS);
-      bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag,
+      bisect_body(ex, dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, q.tol, theta + t, flag,
                   &sh);
     }
     return FST_OK;
@@ -151,7 +146,7 @@ struct EmuRunner : Runner {
                          int *flag) override {
     for (int t = 0; t < nt; ++t) {
       const TargetDesc &q = td[t];
-      bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, theta + t, flag);
+      bisect1_body(dcat + q.mat_off, e2cat + q.mat_off, q.n, q.target, q.glo, q.ghi, q.pivmin, q.tol, theta + t, flag);
     }
     return FST_OK;
   }

@@ -579,7 +579,9 @@ static fst_status batched_window_vectors(std::vector<PendingWin *> &grp) {
         q.glo = glo - widen;
         q.ghi = ghi + widen;
         q.pivmin = pivmin;
-        q.tol = 2.220446049250313e-16 * tnorm + pivmin;   // > 0 also for a zero matrix (N = 1)
+        // pivot lift of the inverse iteration and absolute floor of the bisection's stopping
+        // test; > 0 also for a zero matrix (N = 1)
+        q.tol = 2.220446049250313e-16 * tnorm + pivmin;
         td.push_back(q);
       }
     }
@@ -644,37 +646,13 @@ static fst_status window_vectors(fst_plan_t p, int64_t lo, int64_t hi, double *S
   return window_eigenvalues(p, S, (int)(hi - lo + 1), lam_host, spec_unit);
 }
 
-static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
-                             double alpha) {
-  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
-  *out = nullptr;
-  if (!(N >= 1 && N <= (1LL << 23))) { delete R; return fail(FST_EINVAL, "need 1 <= N <= 2^23"); }
-  if (!(W > 0.0 && W < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < W < 1/2"); }
-  if (!(eps > 0.0 && eps < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < eps < 1/2"); }
-  if (op < 0 || op > 2) { delete R; return fail(FST_EINVAL, "unknown operator"); }
-  if (op == FST_OP_TIKHONOV && !(alpha > 0.0)) { delete R; return fail(FST_EINVAL, "Tikhonov needs alpha > 0"); }
-  const int64_t Kdef = (int64_t)floor(2.0 * (double)N * W + 0.5);
-  if (K < 0) K = Kdef;
-  if (K > N) { delete R; return fail(FST_EINVAL, "need 0 <= K <= N"); }
-
-  fst_plan_t p = new fst_plan_s();
-  p->R = R;
-  p->N = N;
-  p->W = W;
-  p->K = K;
-  p->eps = eps;
-  p->op = op;
-  p->alpha = (op == FST_OP_TIKHONOV) ? alpha : 0.0;
-  p->beta = (op == FST_OP_TIKHONOV) ? 1.0 / (1.0 + alpha) : 1.0;
-  int64_t M = 2;
-  while (M < 2 * N) M *= 2;
-  p->M = M;
-  p->log2M = ilog2_exact(M);
-
-  auto bail = [&](fst_status s) {
-    destroy_plan(p);
-    return s;
-  };
+static fst_status plan_fill(fst_plan_t p) {
+  Runner *R = p->R;
+  const int64_t N = p->N, M = p->M;
+  const double W = p->W;
+  // errors return straight away: the caller destroys the plan once every scoped buffer here
+  // has been released (they need the plan's runner)
+  auto bail = [](fst_status s) { return s; };
 
   // twiddle tables (FP64, rounded copy for FP32)
   {
@@ -780,6 +758,41 @@ static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, in
     if ((s = R->spec_store(X, L64, L32, M, p->beta / (double)M, p->spec64, p->spec32)) != FST_OK) return bail(s);
   }
 
+  return FST_OK;
+}
+
+static fst_status plan_begin(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                             double alpha) {
+  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
+  *out = nullptr;
+  if (!(N >= 1 && N <= (1LL << 23))) { delete R; return fail(FST_EINVAL, "need 1 <= N <= 2^23"); }
+  if (!(W > 0.0 && W < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < W < 1/2"); }
+  if (!(eps > 0.0 && eps < 0.5)) { delete R; return fail(FST_EINVAL, "need 0 < eps < 1/2"); }
+  if (op < 0 || op > 2) { delete R; return fail(FST_EINVAL, "unknown operator"); }
+  if (op == FST_OP_TIKHONOV && !(alpha > 0.0)) { delete R; return fail(FST_EINVAL, "Tikhonov needs alpha > 0"); }
+  const int64_t Kdef = (int64_t)floor(2.0 * (double)N * W + 0.5);
+  if (K < 0) K = Kdef;
+  if (K > N) { delete R; return fail(FST_EINVAL, "need 0 <= K <= N"); }
+
+  fst_plan_t p = new fst_plan_s();
+  p->R = R;
+  p->N = N;
+  p->W = W;
+  p->K = K;
+  p->eps = eps;
+  p->op = op;
+  p->alpha = (op == FST_OP_TIKHONOV) ? alpha : 0.0;
+  p->beta = (op == FST_OP_TIKHONOV) ? 1.0 / (1.0 + alpha) : 1.0;
+  int64_t M = 2;
+  while (M < 2 * N) M *= 2;
+  p->M = M;
+  p->log2M = ilog2_exact(M);
+
+  fst_status fs = plan_fill(p);
+  if (fs != FST_OK) {
+    destroy_plan(p);
+    return fs;
+  }
   *out = p;
   return FST_OK;
 }
@@ -855,18 +868,17 @@ static fst_status plan_end(fst_plan_t p, double *S, const std::vector<double> &l
 }
 
 static void free_coef(fst_plan_t p);
-fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
-                      double alpha) {
-  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
-  *out = nullptr;
-  fst_plan_t p = nullptr;
-  TRY(plan_begin(R, &p, N, W, K, eps, op, alpha));
+// eigen stage of one plan: window search, vectors, eigenvalues, transition set
+static fst_status plan_eigen(fst_plan_t p) {
+  const int64_t N = p->N;
+  const double W = p->W, eps = p->eps;
+  const int op = p->op;
+  Runner *R = p->R;
+  const int64_t K = p->K;
   const int64_t Kdef = (int64_t)floor(2.0 * (double)N * W + 0.5);
-  K = p->K;
-  auto bail = [&](fst_status s) {
-    destroy_plan(p);
-    return s;
-  };
+  // errors return straight away: the caller destroys the plan after the scoped buffers here
+  // are released
+  auto bail = [](fst_status s) { return s; };
   const double *spec_unit = p->spec_unit;
   Scoped sc(R);
   // eigen-window around the centre, widened until both edges are outside T
@@ -898,8 +910,20 @@ fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K
     if (attempt > 12) return bail(fail(FST_ENOCONVERGE, "eigen-window search did not terminate"));
     Rw *= 2;
   }
-  fst_status st = plan_end(p, S, lamw, lo, hi);
-  if (st != FST_OK) return bail(st);
+  return plan_end(p, S, lamw, lo, hi);
+}
+
+fst_status build_plan(Runner *R, fst_plan_t *out, int64_t N, double W, int64_t K, double eps, int op,
+                      double alpha) {
+  if (!out) { delete R; return fail(FST_EINVAL, "out is NULL"); }
+  *out = nullptr;
+  fst_plan_t p = nullptr;
+  TRY(plan_begin(R, &p, N, W, K, eps, op, alpha));
+  const fst_status st = plan_eigen(p);
+  if (st != FST_OK) {
+    destroy_plan(p);
+    return st;
+  }
   *out = p;
   return FST_OK;
 }
@@ -1779,7 +1803,7 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
     fst_plan_t p = plans[i];
     const Layout &L = dbl ? p->lay64 : p->lay32;
     if (L.small) {
-      RaggedDesc<T> d{};
+      RaggedDesc<T> d;
       d.y = (const T *)y[i];
       d.out = (T *)out[i];
       d.spec = (const T *)(dbl ? (const void *)p->spec64 : (const void *)p->spec32);
@@ -1792,29 +1816,6 @@ static fst_status ragged_t(const fst_plan_t *plans, const void *const *y, void *
       maxr[p->log2M] = std::max(maxr[p->log2M], (int)p->rpad);
     } else {
       others.push_back(i);
-    }
-  }
-  // real signals share a CTA two at a time (the second as the imaginary part, its own spectrum
-  // and correction)
-  if (!cplx) {
-    for (auto &b : buckets) {
-      std::vector<RaggedDesc<T>> pb;
-      for (size_t k = 0; k < b.size(); k += 2) {
-        RaggedDesc<T> d = b[k];
-        if (k + 1 < b.size()) {
-          const RaggedDesc<T> &e = b[k + 1];
-          d.y2 = e.y;
-          d.out2 = e.out;
-          d.spec2 = e.spec;
-          d.ST2 = e.ST;
-          d.D2 = e.D;
-          d.N2 = e.N;
-          d.r2 = e.r;
-          d.rpad2 = e.rpad;
-        }
-        pb.push_back(d);
-      }
-      b.swap(pb);
     }
   }
   for (int lg = 0; lg < 32; ++lg) {

@@ -166,14 +166,6 @@ template <typename T> struct RaggedDesc {
   const T *D;
   int64_t N;
   int r, rpad;
-  // a second real signal of the same FFT length in the same CTA (y2 == nullptr: none)
-  const T *y2;
-  T *out2;
-  const T *spec2;
-  const T *ST2;
-  const T *D2;
-  int64_t N2;
-  int r2, rpad2;
 };
 
 template <typename T> struct KState {
@@ -300,96 +292,6 @@ FST_HD void small_body(Ex &ex, const ConvArgs<T> &a, int64_t pl, c2<T> *buf, T *
       c2<T> v = buf[pad(i)];
       if (corr) v = cadd(v, corr_value(a, i, coef, coef + a.rpad));
       store_pair(a, pl, i, v);
-    }
-  });
-}
-
-// ---- small, two real signals with their own plans (ragged batches) ----------------
-// x = y_a + i y_b, X = FFT(x): with C_a, C_b the two spectra (real, even), the filtered spectrum
-// C_a Ya + i C_b Yb is Z[k] = (C_a + C_b)/2 X[k] + (C_a - C_b)/2 conj X[M - k], so IFFT(Z) =
-// B_a y_a + i B_b y_b.  Each signal's coefficients a = D o S_T^T y come from its own S_T and D
-// (read from the input in shared memory before the transform); S_T a is added on the way out.
-// smem as small_body; coef holds a_a at [0, rpad) and a_b at [rpad, rpad + rpad2).
-template <typename T, typename Ex>
-FST_HD void small_pair_body(Ex &ex, const ConvArgs<T> &a, const RaggedDesc<T> &q, c2<T> *buf, T *red, T *coef) {
-  using St = typename Ex::State;
-  const int log2L = a.log2M;
-  const int L = 1 << log2L;
-  const int nthr = ex.nthr;
-  const int nwarps = (nthr + 31) / 32;
-  const int Na = (int)q.N, Nb = (int)q.N2;
-  ex.phase([&](int tid, St &) {
-    for (int i = tid; i < L; i += nthr)
-      buf[pad(i)] = mk<T>(i < Na ? q.y[i] : (T)0, i < Nb ? q.y2[i] : (T)0);
-  });
-  T *const cfs[2] = {coef, coef + q.rpad};
-  for (int s = 0; s < 2; ++s) {
-    const T *ST = s ? q.ST2 : q.ST;
-    const T *D = s ? q.D2 : q.D;
-    const int r = s ? q.r2 : q.r, rpad = s ? q.rpad2 : q.rpad, N = s ? Nb : Na;
-    T *cf = cfs[s];
-    for (int j0 = 0; j0 < r; j0 += 64) {
-      // warps split the samples, lanes split j: red[w][jj] = sum over the warp's samples
-      ex.phase([&](int tid, St &) {
-        const int w = tid >> 5, lane = tid & 31;
-        T acc0 = 0, acc1 = 0;
-        const int ja = j0 + lane, jb = j0 + lane + 32;
-        for (int i = w; i < N; i += nwarps) {
-          const c2<T> v = buf[pad(i)];
-          const T x = s ? v.y : v.x;
-          const T *row = ST + (int64_t)i * rpad;
-          const T sa = (ja < r) ? ldg(row + ja) : (T)0;
-          const T sb = (jb < r) ? ldg(row + jb) : (T)0;
-          acc0 += sa * x;
-          acc1 += sb * x;
-        }
-        T *rw = red + w * 128;
-        rw[lane] = acc0;
-        rw[32 + lane] = acc1;
-      });
-      ex.phase([&](int tid, St &) {
-        for (int t = tid; t < 64; t += nthr) {
-          T sum = 0;
-          for (int w = 0; w < nwarps; ++w) sum += red[w * 128 + t];
-          const int j = j0 + t;
-          if (j < r) cf[j] = ldg(D + j) * sum;
-        }
-      });
-    }
-  }
-
-  tile_fft<T, false>(ex, buf, log2L, 1, a.tw);
-
-  // Z for k and its mirror M - k by one thread (in place; k = 0 and M/2 mirror themselves)
-  ex.phase([&](int tid, St &) {
-    for (int k = tid; k <= L / 2; k += nthr) {
-      const int m = (L - k) & (L - 1);
-      const c2<T> xk = buf[pad(k)], xm = buf[pad(m)];
-      const T cak = ldg(q.spec + k), cbk = ldg(q.spec2 + k);
-      const T Ak = (T)0.5 * (cak + cbk), Bk = (T)0.5 * (cak - cbk);
-      if (m != k) {
-        const T cam = ldg(q.spec + m), cbm = ldg(q.spec2 + m);
-        const T Am = (T)0.5 * (cam + cbm), Bm = (T)0.5 * (cam - cbm);
-        buf[pad(m)] = mk<T>(Am * xm.x + Bm * xk.x, Am * xm.y - Bm * xk.y);
-      }
-      buf[pad(k)] = mk<T>(Ak * xk.x + Bk * xm.x, Ak * xk.y - Bk * xm.y);
-    }
-  });
-
-  tile_fft<T, true>(ex, buf, log2L, 1, a.tw);
-
-  ex.phase([&](int tid, St &) {
-    for (int i = tid; i < Na; i += nthr) {
-      T v = buf[pad(i)].x;
-      const T *row = q.ST + (int64_t)i * q.rpad;
-      for (int j = 0; j < q.r; ++j) v += ldg(row + j) * cfs[0][j];
-      q.out[i] = v;
-    }
-    for (int i = tid; i < Nb; i += nthr) {
-      T v = buf[pad(i)].y;
-      const T *row = q.ST2 + (int64_t)i * q.rpad2;
-      for (int j = 0; j < q.r2; ++j) v += ldg(row + j) * cfs[1][j];
-      q.out2[i] = v;
     }
   });
 }

@@ -78,10 +78,13 @@ struct BisectShared {
 
 // Block computes the eigenvalue of ascending index `target` of the reduced matrix:
 // each round evaluates the Sturm count at 64 interior points of [lo, hi] and keeps
-// the sub-interval that holds it (6 bits per round).  flag != 0 on non-convergence.
+// the sub-interval that holds it (6 bits per round), until the interval is within 4 ulp
+// of its ends plus abstol (about eps ||T||: an eigenvalue near 0, e.g. every transition
+// eigenvalue at W = 1/4 where the diagonal vanishes, needs no more for the inverse
+// iteration).  flag != 0 on non-convergence.
 template <typename Ex>
 FST_HD void bisect_body(Ex &ex, const double *d, const double *e2, int n, int target, double glo, double ghi,
-                        double pivmin, double *out, int *flag, BisectShared *sh) {
+                        double pivmin, double abstol, double *out, int *flag, BisectShared *sh) {
   using St = typename Ex::State;
   ex.phase([&](int tid, St &) {
     if (tid == 0) { sh->lo = glo; sh->hi = ghi; sh->done = 0; }
@@ -102,7 +105,7 @@ FST_HD void bisect_body(Ex &ex, const double *d, const double *e2, int n, int ta
         const double nhi = (t == BISECT_THREADS) ? hi : lo + (hi - lo) * (double)(t + 1) / (double)(BISECT_THREADS + 1);
         sh->lo = nlo;
         sh->hi = nhi;
-        const double tol = 4.0 * 2.220446049250313e-16 * fmax(fabs(nlo), fabs(nhi)) + pivmin;
+        const double tol = 4.0 * 2.220446049250313e-16 * fmax(fabs(nlo), fabs(nhi)) + abstol;
         if (nhi - nlo <= tol || (nlo == lo && nhi == hi)) sh->done = 1;
       }
     });
@@ -120,11 +123,11 @@ FST_HD void bisect_body(Ex &ex, const double *d, const double *e2, int n, int ta
 // once: the throughput of thousands of independent targets matters more than the
 // latency of one.  flag != 0 if it did not converge.
 FST_HD void bisect1_body(const double *d, const double *e2, int n, int target, double glo, double ghi, double pivmin,
-                         double *out, int *flag) {
+                         double abstol, double *out, int *flag) {
   double lo = glo, hi = ghi;
   int it = 0;
   for (; it < 256; ++it) {
-    const double tol = 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
+    const double tol = 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + abstol;
     if (hi - lo <= tol) break;
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;

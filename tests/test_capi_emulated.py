@@ -79,7 +79,9 @@ def test_reduced_tridiagonal_split(N, W):
 
 
 EMU_CASES = [(1, 0.3, 1e-6), (2, 0.3, 1e-6), (5, 0.2, 1e-3), (64, 0.2, 1e-3), (257, 0.11, 1e-6),
-             (1000, 1 / 64, 1e-8), (4096, 1 / 16, 1e-6), (9000, 0.05, 1e-6), (20000, 0.2, 1e-4)]
+             (1000, 1 / 64, 1e-8), (4096, 1 / 16, 1e-6), (9000, 0.05, 1e-6), (20000, 0.2, 1e-4),
+             # W = 1/4: the tridiagonal's diagonal vanishes (cos 2 pi W = 0); W > 1/4: it is negative
+             (3001, 0.25, 1e-6), (777, 0.45, 1e-8)]
 
 
 @pytest.mark.parametrize("N,W,eps", EMU_CASES)
@@ -338,9 +340,9 @@ def test_emulated_plan_many_and_ragged_projection():
             assert np.linalg.norm(o - O.fast_project(op, y)) <= tol * np.linalg.norm(y)
 
 
-def test_emulated_ragged_small_signals_share_ctas():
-    # real single-CTA signals of one FFT length go two to a CTA (the second as the imaginary
-    # part, its own spectrum and correction); an odd count leaves one alone; ranks differ
+def test_emulated_ragged_small_signals_one_length_class():
+    # five single-CTA signals of one FFT length (M = 4096) with their own plans and ranks,
+    # against the oracle, and the in-place call equal to the out-of-place one
     params = [(1100, 0.05, 1e-3), (1500, 0.2, 1e-8), (2048, 0.1, 1e-6), (1025, 0.3, 1e-4), (1800, 0.02, 1e-6)]
     ps = F.PlanSet(params, emulate=True)
     rng = np.random.default_rng(4)

@@ -42,7 +42,8 @@ def rel_err(out, ref, y):
 # ---------------------------------------------------------------- plan ------------
 
 @pytest.mark.parametrize("N,W,eps", [(4096, 1 / 16, 1e-6), (65536, 1 / 8, 1e-4), (1000, 1 / 64, 1e-8),
-                                     (12345, 0.3, 1e-3), (777, 0.45, 1e-12), (1, 0.3, 1e-6), (2, 0.1, 1e-6)])
+                                     (12345, 0.3, 1e-3), (777, 0.45, 1e-12), (1, 0.3, 1e-6), (2, 0.1, 1e-6),
+                                     (3001, 0.25, 1e-6), (40000, 0.25, 1e-8)])   # W = 1/4: zero diagonal
 def test_plan_matches_oracle(N, W, eps):
     _cuda()
     p = F.Plan(N, W, eps=eps)
