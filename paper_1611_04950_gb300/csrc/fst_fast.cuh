@@ -197,6 +197,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
@@ -375,13 +381,15 @@ __device__ __forceinline__ void tw_table16(const float2 *tab, int ldk, int k, bo
 //   row4096_fwd: forward DFT of `row` (global) -> x[t] = X[j + 256 t] (natural order)
 //   row4096_inv: inverse DFT of x[t] = Z[j + 256 t] -> x[t] = z[j + 256 t]
 //   row4096_store: row[j + 256 t] = x[t] W_M^{-n2 k1}, n2 = j + 256 t
-template <bool COHERENT = false>
+template <bool COHERENT = false, bool SMEM_IN = false>
 __device__ __forceinline__ void row4096_fwd(const float2 *row, float2 *buf, const float2 *twB, int j, float2 *x) {
   constexpr int T = 256;
-  // stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory
+  // stage 1 (Ns = 1): inputs x[j + 256 t] straight from global memory (SMEM_IN: already copied
+  // to buf[pad(n)], read before the stage's writes)
 #pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = row[j + T * t];
+  for (int t = 0; t < 16; ++t) x[t] = SMEM_IN ? buf[pad(j + T * t)] : row[j + T * t];
   Dft<float, 16, false>::run(x);
+  if (SMEM_IN) __syncthreads();
 #pragma unroll
   for (int t = 0; t < 16; ++t) buf[pad(16 * j + t)] = x[t];
   __syncthreads();
@@ -497,8 +505,23 @@ __global__ void __launch_bounds__(256, 3) k_fastB4096_2s(const ConvArgs<float> a
   const RPair<float> &q = a.rp[a.pair0 + pl];
   const float *ca = q.spec, *cb = q.spec2 ? q.spec2 : q.spec;
   float2 *row0 = a.inter + (pl * P + r0) * (int64_t)Q;
+  float2 *row1 = a.inter + (pl * P + r1) * (int64_t)Q;
+  // both rows' inputs in flight at once: 8-byte copies into the padded layout
+  {
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(buf0), s1 = (uint32_t)__cvta_generic_to_shared(buf1);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) cp_async8(s0 + (uint32_t)(pad(j + T * t) * 8), row0 + j + T * t);
+    cp_async_commit();
+    if (r1 != r0) {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) cp_async8(s1 + (uint32_t)(pad(j + T * t) * 8), row1 + j + T * t);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait1();
+  __syncthreads();
   float2 x[16];
-  row4096_fwd<true>(row0, buf0, a.twB, j, x);
+  row4096_fwd<true, true>(row0, buf0, a.twB, j, x);
   __syncthreads();   // the last stage's reads of buf0 are done
 #pragma unroll
   for (int t = 0; t < 16; ++t) buf0[pad(j + T * t)] = x[t];
@@ -515,8 +538,9 @@ __global__ void __launch_bounds__(256, 3) k_fastB4096_2s(const ConvArgs<float> a
     row4096_store(row0, a.tw, a.log2M, r0, j, x);
     return;
   }
-  float2 *row1 = a.inter + (pl * P + r1) * (int64_t)Q;
-  row4096_fwd<true>(row1, buf1, a.twB, j, x);
+  cp_async_wait0();
+  __syncthreads();
+  row4096_fwd<true, true>(row1, buf1, a.twB, j, x);
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < 16; ++t) buf1[pad(j + T * t)] = x[t];
@@ -1176,12 +1200,6 @@ constexpr int RC_U = 4, RC_NST = 3;
 constexpr int RC_S_F = 256 * RC_U * 4;            // S floats per tile (1024 float4 at most)
 constexpr int RC_STAGE_F = RC_S_F + 4 * 512;      // + y: up to 512 rows x (re, im) x (n, N-1-n)
 constexpr int rcorr_smem() { return RC_NST * RC_STAGE_F * 4; }
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_ring() {
   asm volatile("cp.async.wait_group %0;" ::"n"(RC_NST - 1) : "memory");
 }
