@@ -483,8 +483,10 @@ __global__ void __launch_bounds__(256, 4) k_fastB4096(const ConvArgs<float> a) {
 //   Z[k] = (Ca + Cb)/2 X[k] + (Ca - Cb)/2 conj X[-k],
 // and IFFT(Z) = (B_a ya) + i (B_b yb) (Ca, Cb real and even).  For k = k1 + P k2 the index -k
 // lies in row P - k1, column Q - 1 - k2 (row 0: column (Q - k2) mod Q).  A CTA takes rows
-// r0 = blockIdx.x and r1 = P - r0 (rows 0 and P/2 pair with themselves): both forward
-// transforms land in shared memory, each thread then forms Z for an index and its mirror in
+// r0 = blockIdx.x and r1 = P - r0 (rows 0 and P/2 pair with themselves): both rows' inputs are
+// copied into shared memory with cp.async up front (the second row's load overlaps the first
+// row's transform), both forward transforms land in shared memory, each thread then forms Z for
+// an index and its mirror in
 // place (the map k2 -> Q - 1 - k2 pairs the two buffers one to one), and the two inverse
 // transforms follow one after the other.
 // grid (P/2 + 1, slots), 256 threads, dynamic shared memory 2 padded_size(4096) float2.
