@@ -78,6 +78,9 @@ typedef enum {
  *   eps     tolerance, 0 < eps < 1/2 (Theorem 1, Corollary 2).
  *   stream  stream for the plan-time kernels; the call synchronises it.
  * K need not satisfy the band condition of Corollary 2; T then grows.
+ * Cost: the Sturm counts and the tridiagonal LU are serial over the N/2 entries of
+ * a reduced matrix, in FP64 (both parities of the window in one batch of targets);
+ * on a GB300 about 0.16 s at N = 65536, 2.6 s at N = 2^20 and 10-13 s at N = 2^22.
  * Errors: FST_EINVAL, FST_ENOMEM, FST_ECUDA, FST_ENOCONVERGE.
  */
 fst_status fst_plan(fst_plan_t *out, int64_t N, double W, int64_t K, double eps,
@@ -215,7 +218,8 @@ fst_status fst_adi_shifts(int64_t N, int r, double *out);
  * fst_plan_many -- count plans at once (ragged batches: one plan per signal).
  * Same precomputation as fst_plan for each (N[i], W[i], K[i] or round(2NW) when
  * K is NULL or K[i] < 0, eps[i]), projection operator; the bisection and inverse
- * iteration of all plans' eigen-windows run as one batch of independent targets.
+ * iteration of all plans' eigen-windows run as one batch of independent targets
+ * (about 35 s for 4096 plans with N log-uniform in [1000, 262144] on a GB300).
  * out[count] receives the plans (destroy each with fst_destroy).  On error every
  * plan of the call is freed and out[] is NULL.  Synchronous.
  */
