@@ -1250,10 +1250,11 @@ extern "C" int fst_profile_count(void) { return (int)g_prof.size(); }
 // copy streams while the previous / next chunk is projected on `stream`
 // ---------------------------------------------------------------------------
 namespace {
+constexpr int HP_SLOTS = 4;   // chunks in flight: copy in, compute and copy out overlap freely
 struct HostPipe {
   cudaStream_t cin = nullptr, cout = nullptr;
-  cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
-  void *din[2] = {}, *dout[2] = {};
+  cudaEvent_t in_done[HP_SLOTS] = {}, comp_done[HP_SLOTS] = {}, out_done[HP_SLOTS] = {};
+  void *din[HP_SLOTS] = {}, *dout[HP_SLOTS] = {};
   size_t slot_bytes = 0;
   int dev = -1;
 };
@@ -1287,7 +1288,7 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
   CU(cudaGetDevice(&dev), "cudaGetDevice");
   if (!g_pipe || g_pipe->dev != dev || g_pipe->slot_bytes < slot) {
     if (g_pipe) {
-      for (int i = 0; i < 2; ++i) {
+      for (int i = 0; i < HP_SLOTS; ++i) {
         cudaFree(g_pipe->din[i]);
         cudaFree(g_pipe->dout[i]);
       }
@@ -1297,13 +1298,13 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
     if (!g_pipe->cin) {
       CU(cudaStreamCreateWithFlags(&g_pipe->cin, cudaStreamNonBlocking), "stream");
       CU(cudaStreamCreateWithFlags(&g_pipe->cout, cudaStreamNonBlocking), "stream");
-      for (int i = 0; i < 2; ++i) {
+      for (int i = 0; i < HP_SLOTS; ++i) {
         CU(cudaEventCreateWithFlags(&g_pipe->in_done[i], cudaEventDisableTiming), "event");
         CU(cudaEventCreateWithFlags(&g_pipe->comp_done[i], cudaEventDisableTiming), "event");
         CU(cudaEventCreateWithFlags(&g_pipe->out_done[i], cudaEventDisableTiming), "event");
       }
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < HP_SLOTS; ++i) {
       g_pipe->din[i] = g_pipe->dout[i] = nullptr;
       CU(cudaMalloc(&g_pipe->din[i], slot), "cudaMalloc");
       CU(cudaMalloc(&g_pipe->dout[i], slot), "cudaMalloc");
@@ -1317,12 +1318,30 @@ extern "C" fst_status fst_project_host(fst_plan_t p, const void *y, void *out, i
   // the copies must not start before earlier work on the compute stream is done
   CU(cudaEventRecord(hp.comp_done[0], sc), "event");
   CU(cudaStreamWaitEvent(hp.cin, hp.comp_done[0], 0), "wait");
-  int64_t i = 0;
-  for (int64_t b0 = 0; b0 < batch; b0 += per, ++i) {
-    const int k = (int)(i & 1);
-    const int64_t nb = std::min<int64_t>(per, batch - b0);
+  // chunk schedule: a short first chunk (compute starts after less copying), full chunks, and a
+  // short last chunk (less copying after the last compute); every chunk but the last has an even
+  // size, so real signals pair as in one call over the whole batch
+  std::vector<int64_t> sizes;
+  const int64_t small = std::max<int64_t>(2, (per / 4) / 2 * 2);
+  if (per >= 8 && batch >= 2 * per + 2 * small) {
+    const int64_t tail = small + (batch & 1);
+    int64_t mid = batch - small - tail;
+    sizes.push_back(small);
+    while (mid > per) {
+      sizes.push_back(per);
+      mid -= per;
+    }
+    if (mid > 0) sizes.push_back(mid);
+    sizes.push_back(tail);
+  } else {
+    for (int64_t b0 = 0; b0 < batch; b0 += per) sizes.push_back(std::min<int64_t>(per, batch - b0));
+  }
+  int64_t b0 = 0;
+  for (size_t i = 0; i < sizes.size(); b0 += sizes[i], ++i) {
+    const int k = (int)(i % HP_SLOTS);
+    const int64_t nb = sizes[i];
     const size_t bytes = (size_t)nb * sig_bytes;
-    if (i >= 2) CU(cudaStreamWaitEvent(hp.cin, hp.out_done[k], 0), "wait");
+    if (i >= (size_t)HP_SLOTS) CU(cudaStreamWaitEvent(hp.cin, hp.out_done[k], 0), "wait");
     CU(cudaMemcpyAsync(hp.din[k], (const char *)y + b0 * sig_bytes, bytes, cudaMemcpyHostToDevice, hp.cin), "h2d");
     CU(cudaEventRecord(hp.in_done[k], hp.cin), "event");
     CU(cudaStreamWaitEvent(sc, hp.in_done[k], 0), "wait");
