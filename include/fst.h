@@ -149,7 +149,7 @@ fst_status fst_project(fst_plan_t plan, const void *y, void *out, int64_t batch,
  * first and last chunks are a quarter of the others); returns after the result is
  * in `out` (synchronous).  Pinned host memory gives the full link bandwidth.  The
  * results are bit-for-bit those of fst_project on the whole batch.  Device scratch:
- * eight chunk buffers of FST_HOST_CHUNK_MB (default 64) MiB, allocated on the first
+ * eight chunk buffers of up to FST_HOST_CHUNK_MB (default 64) MiB, allocated on the first
  * call of a thread and kept for its later calls.
  */
 fst_status fst_project_host(fst_plan_t plan, const void *y, void *out, int64_t batch,
