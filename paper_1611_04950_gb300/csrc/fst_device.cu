@@ -822,6 +822,8 @@ struct DevRunner : Runner {
   fst_status reduce(const ConvArgs<float> &a, const Layout &L) override { return reduce_t(a, L); }
   fst_status reduce(const ConvArgs<double> &a, const Layout &L) override { return reduce_t(a, L); }
   fst_status passB(const ConvArgs<float> &a, const Layout &L) override {
+    if (a.two_spec && !((L.fast || L.big) && L.log2Q == 12))
+      return fail(FST_EINVAL, "two-spectrum row pass needs 4096-point rows");
     if ((L.fast || L.big) && L.log2Q == 13 && a.tw8) {
       TRY(set_attrs());
       dim3 grid((unsigned)(1u << L.log2P), (unsigned)a.npairs);
